@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of exact sparse products over Z/mZ on one GB300 (or N replicas).
+
+Workload (one step): y = A*x and z = A^T*x (mod m) on the 1M x 1M power-law
+matrix (Zipf row lengths, mean 16, max 10 000, ~15.8M nonzeros, uniform
+distinct columns), m = 65521, through the library's plan.  Inputs are
+resident in HBM; L2 is flushed (a 256 MB write) between timed steps, outside
+the timed events.  Throughput is Gnnz*vec/s: nonzeros times vectors per
+second (the paper's Mflops / 2000).
+
+Also printed, in the same JSON line:
+  roofline      achieved algorithmic GB/s of the A*x kernel vs measured HBM peak
+  e2e           the same step with x on pinned host memory and y, z copied back
+  cpu_baseline  the CPU oracle on this host (bounded sample)
+  clocks        SM clocks sampled during the timed region
+  extra         other formats and moduli, the block Wiedemann sequence
+                (persistent kernel vs one launch per kernel), the batched launch
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "mod-p SpMV Gnnz*vec/s"
+UNIT = "Gnnz*vec/s"
+WORKLOAD = ("powerlaw 1M x 1M, Zipf row lengths mean 16 max 10k (15.8M nnz), m=65521; "
+            "step = y=A*x and z=A^T*x")
+SEED = 1002
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--modulus", type=int, default=65521)
+    ap.add_argument("--format", default="AUTO")
+    ap.add_argument("--extras", default="formats,sequence",
+                    help="comma list from formats,sequence,batch ('' for none)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(A, m):
+    """Sec. 2.1 CSR traffic of one y = A*x: per nonzero a 4-byte column index
+    and a value (2 bytes if m <= 2^16, 4 otherwise), plus 4(n+1) bytes of row
+    pointers, 4n of x and 4n of y."""
+    vb = 2 if m <= 65536 else 4
+    return A.nnz * (4 + vb) + 4 * (A.nrows + 1) + 4 * A.ncols + 4 * A.nrows
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    rec = d.get(kernel_key)
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "plan.cu", "ff_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1004_3719_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(A, x, seconds):
+    """The oracle's y = A x and z = A^T x on this host, repeated for about
+    `seconds` (at least once)."""
+    import oracle
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.csr_spmv(A, x)
+        oracle.csr_spmv_transpose(A, x)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(2 * A.nnz * n / dt / 1e9, 4), "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n} steps (y=A*x, z=A^T*x) on the full matrix, single thread, {dt:.1f} s"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    A = gen.powerlaw_matrix(seed=SEED, m=args.modulus)
+    x = gen.uniform_block(SEED, A.ncols, 1, args.modulus)
+    for _ in range(args.warmup):
+        oracle.csr_spmv(A, x)
+        oracle.csr_spmv_transpose(A, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.csr_spmv(A, x)
+        oracle.csr_spmv_transpose(A, x)
+    dt = time.perf_counter() - t0
+    val = 2 * A.nnz * args.steps / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "modulus": args.modulus},
+        "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed steps of the full workload, single thread"},
+        "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def timed_steps(torch, fn, steps, flush, stream):
+    """Sum of per-step device times (ms), L2 flushed before every step."""
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
+    out = {}
+    fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED"]
+    for m in moduli:
+        A = gen.powerlaw_matrix(seed=SEED, m=m)
+        x = torch.from_numpy(gen.uniform_block(SEED, A.ncols, 1, m).view(np.int32)).cuda()
+        y = torch.empty(A.nrows, dtype=torch.int32, device="cuda")
+        row = {}
+        for f in fmts:
+            for pm in ((0, 1) if m == 3 else (-1,)):
+                key = f if pm < 0 else f"{f}{'+pm1' if pm else '-nopm1'}"
+                try:
+                    M = ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, f),
+                                           transpose_mode=ff.TRANSPOSE.NONE, use_pm1=pm)
+                except ff.FFSPMVError as e:
+                    row[key] = f"n/a ({e.status == 5 and 'size guard' or e})"
+                    continue
+                fn = lambda: ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, stream)
+                for _ in range(3):
+                    fn()
+                t = timed_steps(torch, fn, 10, flush, stream)
+                ms = statistics.median(t)
+                row[key] = {"gnnz_s": round(A.nnz / ms / 1e6, 1),
+                            "gbs": round(algorithmic_bytes(A, m) / ms / 1e6, 1),
+                            "ms": round(ms, 4)}
+                del M
+        out[f"m={m}"] = row
+    return out
+
+
+def extra_sequence(torch, ff, stream):
+    p, s = 65521, 16
+    W = gen.wiedemann_matrix(seed=1003)
+    n = W.nrows
+    L = 2 * n // s + 2
+    X = torch.from_numpy(gen.uniform_block(1003, n, s, p).view(np.int32)).cuda()
+    Y = torch.from_numpy(gen.uniform_block(1003, n, s, p, key=1).view(np.int32)).cuda()
+    res = {"workload": f"wiedemann 100k x 100k ({W.nnz} nnz), s=16, p=65521, {L} steps"}
+    for mode, name in ((0, "persistent_graph"), (1, "per_launch")):
+        M = ff.Matrix.from_csr(W, sequence_mode=mode, transpose_mode=ff.TRANSPOSE.NONE)
+        S = torch.empty((L, s, s), dtype=torch.int32, device="cuda")
+        ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3 if mode == 0 else 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = min(ts)
+        res[name] = {"ms": round(ms, 3), "us_per_step": round(ms * 1e3 / L, 3),
+                     "gnnz_vec_s": round(W.nnz * s * (L - 1) / ms / 1e6, 1)}
+        del M
+    return res
+
+
+def extra_batch(torch, ff, stream):
+    probs = gen.batch_problems(seed=1004)
+    mats = [ff.Matrix.from_csr(A, transpose_mode=ff.TRANSPOSE.NONE, priority_format=ff.FMT.CSR)
+            for A, _ in probs]
+    xs = [torch.from_numpy(np.ascontiguousarray(
+        gen.uniform_block(7 + j, A.ncols, s, A.modulus)).view(np.int32)).cuda()
+        for j, (A, s) in enumerate(probs)]
+    ys = [torch.empty((A.nrows, s) if s > 1 else (A.nrows,), dtype=torch.int32, device="cuda")
+          for A, s in probs]
+    nv = [s for _, s in probs]
+    work = sum(A.nnz * s for A, s in probs)
+
+    def one_launch():
+        ff.spmv_batch_apply([M.handle for M in mats], xs, ys, nv, stream)
+
+    def per_matrix():
+        for M, x, y, s in zip(mats, xs, ys, nv):
+            ff.spmv_apply(M.handle, x, s, y, s, s, 1, 0, stream)
+
+    res = {"workload": f"{len(probs)} matrices, {sum(A.nnz for A, _ in probs)} nnz, "
+                       f"{work} nnz*vec per pass"}
+    for name, fn in (("one_launch", one_launch), ("per_matrix_fixed_csr", per_matrix)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        res[name] = {"ms": round(ms, 3), "gnnz_vec_s": round(work / ms / 1e6, 1)}
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_1004_3719_gb300 as ff
+    ff.build()
+    m = args.modulus
+    A = gen.powerlaw_matrix(seed=SEED, m=m)
+    x_host = gen.uniform_block(SEED + rank, A.ncols, 1, m)
+    M = ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, args.format))
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    x = torch.from_numpy(x_host.view(np.int32)).cuda()
+    y = torch.empty(A.nrows, dtype=torch.int32, device="cuda")
+    z = torch.empty(A.ncols, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, sp)
+        ff.spmv_apply_transpose(M.handle, x, 1, z, 1, 1, 1, 0, sp)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, sp)
+        e[1].record(stream)
+        ff.spmv_apply_transpose(M.handle, x, 1, z, 1, 1, 1, 0, sp)
+        e[2].record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_step = [e[0].elapsed_time(e[2]) for e in evs]
+    t_ax = [e[0].elapsed_time(e[1]) for e in evs]
+    total_ms = sum(t_step)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = 2 * A.nnz * args.steps * world
+    value = units / (total_ms / 1e3) / 1e9
+    launches = args.steps * (M.launches(False, 1) + M.launches(True, 1))
+
+    # end to end: x from pinned host memory, y and z back to pinned host memory
+    xh = torch.from_numpy(x_host.view(np.int32)).pin_memory()
+    yh = torch.empty(A.nrows, dtype=torch.int32).pin_memory()
+    zh = torch.empty(A.ncols, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for i in range(max(args.steps // 2, 5) + 2):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.copy_(xh, non_blocking=True)
+        step()
+        yh.copy_(y, non_blocking=True)
+        zh.copy_(z, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = 2 * A.nnz / (statistics.mean(e2e_ms) / 1e3) / 1e9
+
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    ax_ms = statistics.mean(t_ax)
+    abytes = algorithmic_bytes(A, m)
+    achieved = abytes / (ax_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": traffic_record("spmv_A_65521"),
+            "kernel": "k_plan (y=A*x)", "algorithmic_bytes": abytes,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
+            "launch_ms": round(ax_ms, 4)}
+    extra = {"plan": M.describe()}
+    wanted = [e for e in args.extras.split(",") if e]
+    del M
+    torch.cuda.empty_cache()
+    for name, fn in (("formats", lambda: extra_formats(torch, ff, flush, sp)),
+                     ("sequence", lambda: extra_sequence(torch, ff, sp)),
+                     ("batch", lambda: extra_batch(torch, ff, sp))):
+        if name in wanted:
+            try:
+                extra[name] = fn()
+            except Exception as e:  # report, do not hide
+                extra[name] = f"failed: {type(e).__name__}: {e}"
+    cpu = cpu_baseline(A, x_host, args.cpu_seconds) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "format": args.format, "modulus": m,
+                   "l2": "flushed (256 MB write) before every timed step, outside the events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "e2e": {"value": round(e2e_val, 3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * A.ncols, "d2h_bytes_per_step": 4 * (A.nrows + A.ncols)},
+        "gpu_launches": launches, "extra": extra,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,22 @@ def distinct_columns(rng, lengths, ncols, forbid=None, window=None):
     """
     lengths = np.asarray(lengths, dtype=np.int64)
     nrows = lengths.size
+    if window is None and forbid is None and nrows:
+        dense = lengths * 4 > ncols
+        if dense.any():
+            # rows filling a large share of the columns: sample them without
+            # replacement directly, the rest by drawing and redrawing
+            sparse_len = np.where(dense, 0, lengths)
+            r_s, c_s = distinct_columns(rng, sparse_len, ncols)
+            rows_d, cols_d = [r_s], [c_s.astype(np.int64)]
+            for i in np.nonzero(dense)[0]:
+                c = np.sort(rng.choice(ncols, int(lengths[i]), replace=False))
+                rows_d.append(np.full(c.size, i, dtype=np.int64))
+                cols_d.append(c.astype(np.int64))
+            rows = np.concatenate(rows_d)
+            cols = np.concatenate(cols_d)
+            order = np.lexsort((cols, rows))
+            return rows[order], cols[order].astype(np.int32)
     nnz = int(lengths.sum())
     rows = np.repeat(np.arange(nrows, dtype=np.int64), lengths)
     if window is None:
@@ -237,35 +253,48 @@ def wiedemann_matrix(seed=1003, n=100_000, p=M65521, n_random=6):
     return _assemble(n, n, lengths, rows, cols, vals, p, f"wiedemann{n}")
 
 
+def windowed_distinct(rng, lengths, lo, hi, chunk=1 << 16):
+    """Row i gets ``lengths[i]`` distinct sorted columns from [lo[i], hi[i])
+    (windows of at most a few hundred columns): the first ``lengths[i]``
+    positions of a random permutation of the window, row by row in chunks."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    width = int((hi - lo).max()) if lengths.size else 0
+    rows_out, cols_out = [], []
+    for a in range(0, lengths.size, chunk):
+        b = min(lengths.size, a + chunk)
+        keys = rng.random((b - a, width))
+        off = np.arange(width)[None, :]
+        keys[off >= (hi[a:b] - lo[a:b])[:, None]] = 2.0     # outside the window
+        order = np.argsort(keys, axis=1)
+        take = off < lengths[a:b, None]
+        picked = np.sort(np.where(take, order, width + 1), axis=1)
+        r, k = np.nonzero(picked <= width)
+        rows_out.append(r + a)
+        cols_out.append(lo[a:b][r] + picked[r, k])
+    if not rows_out:
+        return np.zeros(0, np.int64), np.zeros(0, np.int32)
+    return np.concatenate(rows_out), np.concatenate(cols_out).astype(np.int32)
+
+
 def banded_matrix(seed, n, lengths, m, bandwidth=64, pm_fraction=0.0):
     rng = rng_for(seed, 6)
     half = bandwidth // 2
-
-    def window(rows):
-        lo = np.maximum(rows - half, 0)
-        hi = np.minimum(rows + half + 1, n)
-        return lo, hi
-
-    lengths = np.minimum(np.asarray(lengths, dtype=np.int64), 2 * half + 1)
-    lengths = np.minimum(lengths, np.minimum(np.arange(n) + half + 1, n) -
-                         np.maximum(np.arange(n) - half, 0))
-    rows, cols = distinct_columns(rng, lengths, n, window=window)
+    i = np.arange(n, dtype=np.int64)
+    lo = np.maximum(i - half, 0)
+    hi = np.minimum(i + half + 1, n)
+    lengths = np.minimum(np.asarray(lengths, dtype=np.int64), hi - lo)
+    rows, cols = windowed_distinct(rng, lengths, lo, hi)
     vals = residues(rng, rows.size, m, pm_fraction)
     return _assemble(n, n, lengths, rows, cols, vals, m, f"banded{n}")
 
 
 def block_diagonal_matrix(seed, n, block, lengths, m, pm_fraction=0.0):
     rng = rng_for(seed, 7)
-
-    def window(rows):
-        lo = (rows // block) * block
-        hi = np.minimum(lo + block, n)
-        return lo, hi
-
-    b0 = (np.arange(n) // block) * block
-    room = np.minimum(b0 + block, n) - b0
-    lengths = np.minimum(np.asarray(lengths, dtype=np.int64), room)
-    rows, cols = distinct_columns(rng, lengths, n, window=window)
+    i = np.arange(n, dtype=np.int64)
+    lo = (i // block) * block
+    hi = np.minimum(lo + block, n)
+    lengths = np.minimum(np.asarray(lengths, dtype=np.int64), hi - lo)
+    rows, cols = windowed_distinct(rng, lengths, lo, hi, chunk=max(1, (1 << 22) // block))
     vals = residues(rng, rows.size, m, pm_fraction)
     return _assemble(n, n, lengths, rows, cols, vals, m, f"blockdiag{n}")
 

@@ -1,0 +1,184 @@
+/*
+ * ffspmv: exact sparse matrix x dense vector / block products over Z/mZ on
+ * GB300 (sm_103a), after Boyer, Dumas and Giorgi, "Exact Sparse
+ * Matrix-Vector Multiplication on GPU's and Multicore Architectures".
+ *
+ * C ABI.  No C++ or PyTorch type appears in a signature.  Pointers named d_*
+ * are CUDA device pointers, h_* host pointers; "host or device" pointers are
+ * detected with cudaPointerGetAttributes.  Every call is asynchronous with
+ * respect to the host and ordered on the `stream` it is given, unless stated
+ * otherwise; errors found on the host are returned before anything is
+ * enqueued.
+ *
+ * Residues are uint32 in [0, m).  All results are the exact representatives in
+ * [0, m); inputs x must already be in [0, m) (checked when
+ * ffspmv_options.value_check = 1, otherwise a larger x gives an unspecified
+ * but memory-safe result).
+ *
+ * Dense blocks of nvec vectors are row-major with a leading dimension:
+ * element (k, v) of X is X[k*ldx + v] (ldx >= nvec).  nvec = 1, ldx = 1 is a
+ * plain vector.  Sec. 2.5.1 leaves the multi-vector layout open; this is the
+ * "one matrix pass, vectors read and written contiguously" form.
+ */
+#ifndef FFSPMV_H
+#define FFSPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ffspmv_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+typedef struct ffspmv_handle *ffspmv_t;       /* opaque; owns all device format data */
+
+typedef enum {
+    FFSPMV_OK = 0,
+    FFSPMV_ERR_ARG = 1,         /* bad argument: null pointer, size, stride, modulus */
+    FFSPMV_ERR_RANGE = 2,       /* an input residue x >= m (value_check = 1) */
+    FFSPMV_ERR_OOM = 3,         /* device or host allocation failed */
+    FFSPMV_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    FFSPMV_ERR_UNSUPPORTED = 5, /* format or size guard refused (e.g. DIA of a random matrix) */
+    FFSPMV_ERR_TIMEOUT = 6      /* a bounded device wait expired (grid barrier) */
+} ffspmv_status;
+
+/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO lets the selector choose. */
+enum {
+    FFSPMV_FMT_AUTO = 0,
+    FFSPMV_FMT_CSR = 1,     /* plain CSR, one fixed thread-group width per row */
+    FFSPMV_FMT_ELLR = 2,    /* ELL_R: column-major ELL + per-row counts (Sec. 2.4.4) */
+    FFSPMV_FMT_COO = 3,     /* coordinate triples, element-parallel segmented sums */
+    FFSPMV_FMT_COOS = 4,    /* COO_S: CSR over the non-empty rows only (Sec. 2.4.5) */
+    FFSPMV_FMT_DIA = 5,     /* diagonals + offsets; refused past a size guard */
+    FFSPMV_FMT_HYBRID = 6,  /* paper heuristic: DIA + ELL_R(w) + CSR/COO/COO_S residue (Sec. 2.4.6) */
+    FFSPMV_FMT_BINNED = 7   /* rows binned by length, one format per bin */
+};
+
+/* Format selectors (how FFSPMV_FMT_AUTO / FFSPMV_FMT_BINNED pick). */
+enum {
+    FFSPMV_SEL_HEURISTIC = 0,  /* the paper's chooser, constants of this library */
+    FFSPMV_SEL_LEARNED = 1,    /* the selector network (ffspmv_selector_load) */
+    FFSPMV_SEL_EXHAUSTIVE = 2, /* time every candidate per bin on the device */
+    FFSPMV_SEL_FIXED = 3       /* use priority_format as is */
+};
+
+/* Transposed products. */
+enum {
+    FFSPMV_TRANSPOSE_EXPLICIT = 0, /* build A^T's plan at create time (default) */
+    FFSPMV_TRANSPOSE_ATOMIC = 1,   /* scatter with exact 64-bit integer atomics */
+    FFSPMV_TRANSPOSE_NONE = 2      /* no transposed product on this handle */
+};
+
+typedef struct {
+    int32_t selector;          /* FFSPMV_SEL_*; default HEURISTIC */
+    int32_t use_pm1;           /* 1: segregate +-1 entries into value-free parts (Sec. 2.4.2); -1 = let the selector decide (default) */
+    int32_t priority_format;   /* FFSPMV_FMT_*; default AUTO */
+    int32_t transpose_mode;    /* FFSPMV_TRANSPOSE_*; default EXPLICIT */
+    int32_t value_check;       /* 1: check x < m on every apply (one extra pass) */
+    int32_t group_width;       /* CSR lanes per row (1..32), 0 = from the mean row length */
+    int32_t ell_width;         /* ELL_R width for HYBRID, -1 = heuristic */
+    uint32_t barrier_spin_limit; /* grid-barrier spins before FFSPMV_ERR_TIMEOUT; 0 = default */
+    int64_t guard_bytes;       /* size guard for ELL_R / DIA storage; 0 = default (32 GiB) */
+    int32_t sequence_mode;     /* block sequence: 0 = persistent kernel when possible, 1 = one launch per kernel per step */
+    int32_t test_hooks;        /* testing only, 0 in normal use: bit 0 = one CTA of the persistent
+                                  sequence kernel never arrives at its first grid barrier, so the
+                                  bounded wait of every other CTA runs out (FFSPMV_ERR_TIMEOUT) */
+} ffspmv_options;
+
+/* Fill *opt with the defaults. */
+void ffspmv_options_default(ffspmv_options *opt);
+
+/*
+ * Build the device plan of an nrows x ncols matrix given in CSR (Sec. 2.1):
+ * row i holds entries row_ptr[i] <= k < row_ptr[i+1], A[i, col[k]] = values[k].
+ * row_ptr: int64[nrows+1] (row_ptr[0] = 0, non-decreasing); col: int32[nnz]
+ * in [0, ncols); values: uint32[nnz], reduced mod m on entry (values >= m are
+ * accepted); repeated (i, j) pairs add up.  The three arrays may be host or
+ * device memory; they are copied and may be freed on return.
+ * modulus: 2 <= m <= 2^32 - 1.  opt: NULL = defaults.  The call is
+ * synchronous (it returns once the plan is resident on the current device).
+ * Format choice follows Sec. 2.4.6 (hybridisation and the heuristic chooser)
+ * or the selector named in opt.  On error *out is NULL and nothing leaks.
+ */
+ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
+                                 int64_t nnz, const int64_t *row_ptr,
+                                 const int32_t *col, const uint32_t *values,
+                                 uint32_t modulus, const ffspmv_options *opt,
+                                 ffspmv_stream_t stream);
+
+/*
+ * Y <- alpha*A*X + beta*Y (mod m), Sec. 2 (the operation y <- alpha A x +
+ * beta y and its block form).  d_x: ncols x nvec (ldx), d_y: nrows x nvec
+ * (ldy); 1 <= nvec; alpha, beta < m (reduced if not).  beta = 0 never reads
+ * d_y ("apply": y <- A x).  d_x and d_y must not overlap.
+ */
+ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx,
+                         uint32_t *d_y, int64_t ldy, int32_t nvec,
+                         uint32_t alpha, uint32_t beta, ffspmv_stream_t stream);
+
+/*
+ * Y <- alpha*A^T*X + beta*Y (mod m): the transpose product (Sec. 1).  d_x:
+ * nrows x nvec, d_y: ncols x nvec.  FFSPMV_ERR_UNSUPPORTED when the handle
+ * was created with FFSPMV_TRANSPOSE_NONE.
+ */
+ffspmv_status spmv_apply_transpose(ffspmv_t h, const uint32_t *d_x,
+                                   int64_t ldx, uint32_t *d_y, int64_t ldy,
+                                   int32_t nvec, uint32_t alpha, uint32_t beta,
+                                   ffspmv_stream_t stream);
+
+/*
+ * The matrix sequence of block Wiedemann (Sec. 3, step 1, with independent
+ * left and right projections): V_0 = Y, V_{i+1} = A*V_i (mod p) and
+ * S_i = X^T * V_i (mod p) for 0 <= i < nsteps, all kept on the device
+ * (Sec. 2.5.2).  A must be square; p is the handle's modulus.
+ * d_X, d_Y: n x s row-major (ld = s), 1 <= s <= 32.  d_S: nsteps x s x s,
+ * S_i[a][b] at d_S[(i*s + a)*s + b].  d_V_next: NULL, or n x s receiving
+ * A^nsteps * Y, from which a later call continues the sequence (checkpoint /
+ * resume).  The steps run as one persistent cooperative kernel captured in a
+ * CUDA graph when the grid fits on the device, else as one graph of
+ * per-step launches.  Synchronises `stream` and returns
+ * FFSPMV_ERR_TIMEOUT if a bounded grid-barrier wait expired.
+ */
+ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X,
+                                  const uint32_t *d_Y, int32_t s,
+                                  int64_t nsteps, uint32_t *d_S,
+                                  uint32_t *d_V_next, ffspmv_stream_t stream);
+
+/*
+ * Independent products Y_j = A_j * X_j (mod m_j), j < count, in one launch
+ * (not in the paper).  hs: host array of handles (each with its own
+ * modulus); d_x / d_y: host arrays of device pointers, X_j: ncols_j x nvec[j]
+ * row-major (ld = nvec[j]), Y_j: nrows_j x nvec[j]; 1 <= nvec[j] <= 32.
+ * The work list is rebuilt on the host only when the set of handles or nvec
+ * changes.
+ */
+ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
+                               const uint32_t *const *d_x,
+                               uint32_t *const *d_y, const int32_t *nvec,
+                               ffspmv_stream_t stream);
+
+/* Free every device buffer of h.  NULL is accepted. */
+ffspmv_status spmv_destroy(ffspmv_t h);
+
+/* Static string naming a status code. */
+const char *ffspmv_status_string(ffspmv_status s);
+
+/* Human-readable summary of the chosen parts, bytes and bins ('\0'-terminated,
+ * truncated to len). */
+ffspmv_status spmv_describe_plan(ffspmv_t h, char *buf, size_t len);
+
+/* Number of kernel launches that one spmv_apply (transpose = 0) or
+ * spmv_apply_transpose (transpose = 1) call with nvec vectors enqueues. */
+ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec,
+                                  int64_t *launches);
+
+/* Matrix shape, nnz, modulus and device bytes of the plan (A and A^T). */
+ffspmv_status spmv_get_info(ffspmv_t h, int64_t *nrows, int64_t *ncols,
+                            int64_t *nnz, uint32_t *modulus,
+                            int64_t *device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFSPMV_H */

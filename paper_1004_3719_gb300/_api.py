@@ -1,0 +1,193 @@
+"""Python names for the C ABI entry points (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import FFSPMVError, Options, check, lib, options_default
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def stream_ptr(stream=None):
+    """The cudaStream_t of a torch stream (default: torch's current one)."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor, a numpy array or an int."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data if a.size else None
+    return a.data_ptr() if a.numel() else None
+
+
+def _as_u32_tensor(a, device):
+    """A 4-byte integer tensor on `device` with the bits of `a` (numpy uint32,
+    int32 or a torch tensor)."""
+    torch = _torch()
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a).view(np.int32))
+    if a.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("residues must be 32-bit integers")
+    return a.to(device).contiguous()
+
+
+def spmv_create_hybrid(nrows, ncols, row_ptr, col, values, modulus, options=None,
+                       stream=None):
+    """Build a plan; arrays may be numpy (host) or torch (host or device)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64) if isinstance(row_ptr, (list, np.ndarray)) else row_ptr
+    col = np.ascontiguousarray(col, dtype=np.int32) if isinstance(col, (list, np.ndarray)) else col
+    values = np.ascontiguousarray(values, dtype=np.uint32) if isinstance(values, (list, np.ndarray)) else values
+    nnz = int(row_ptr[-1]) if len(row_ptr) else 0
+    h = ctypes.c_void_p()
+    opt = options if options is not None else options_default()
+    st = lib().spmv_create_hybrid(ctypes.byref(h), int(nrows), int(ncols), nnz,
+                                  _ptr(row_ptr), _ptr(col), _ptr(values),
+                                  int(modulus), ctypes.byref(opt),
+                                  stream_ptr(stream) if stream is not None else None)
+    check(st, "spmv_create_hybrid")
+    return h
+
+
+def spmv_apply(h, x, ldx, y, ldy, nvec, alpha=1, beta=0, stream=None):
+    check(lib().spmv_apply(h, _ptr(x), int(ldx), _ptr(y), int(ldy), int(nvec),
+                           int(alpha), int(beta), stream_ptr(stream)), "spmv_apply")
+
+
+def spmv_apply_transpose(h, x, ldx, y, ldy, nvec, alpha=1, beta=0, stream=None):
+    check(lib().spmv_apply_transpose(h, _ptr(x), int(ldx), _ptr(y), int(ldy), int(nvec),
+                                     int(alpha), int(beta), stream_ptr(stream)),
+          "spmv_apply_transpose")
+
+
+def spmv_block_sequence(h, X, Y, s, nsteps, S, V_next=None, stream=None):
+    check(lib().spmv_block_sequence(h, _ptr(X), _ptr(Y), int(s), int(nsteps), _ptr(S),
+                                    _ptr(V_next), stream_ptr(stream)),
+          "spmv_block_sequence")
+
+
+def spmv_batch_apply(handles, xs, ys, nvec, stream=None):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    Y = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+    NV = (ctypes.c_int32 * n)(*[int(v) for v in nvec])
+    check(lib().spmv_batch_apply(n, H, X, Y, NV, stream_ptr(stream)), "spmv_batch_apply")
+
+
+def spmv_destroy(h):
+    if h:
+        lib().spmv_destroy(h)
+
+
+def spmv_describe_plan(h):
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib().spmv_describe_plan(h, buf, len(buf)), "spmv_describe_plan")
+    return buf.value.decode()
+
+
+def spmv_get_info(h):
+    v = [ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint32(), ctypes.c_int64()]
+    check(lib().spmv_get_info(h, *[ctypes.byref(t) for t in v]), "spmv_get_info")
+    return dict(nrows=v[0].value, ncols=v[1].value, nnz=v[2].value, modulus=v[3].value,
+                device_bytes=v[4].value)
+
+
+def spmv_count_launches(h, transpose, nvec):
+    n = ctypes.c_int64()
+    check(lib().spmv_count_launches(h, int(transpose), int(nvec), ctypes.byref(n)),
+          "spmv_count_launches")
+    return n.value
+
+
+class Matrix:
+    """An n x m sparse matrix over Z/mZ resident on the current CUDA device."""
+
+    def __init__(self, nrows, ncols, row_ptr, col, values, modulus, options=None, **opts):
+        if options is None:
+            options = options_default(**opts)
+        self.nrows, self.ncols, self.modulus = int(nrows), int(ncols), int(modulus)
+        self.options = options
+        self.handle = spmv_create_hybrid(nrows, ncols, row_ptr, col, values, modulus, options)
+
+    @classmethod
+    def from_csr(cls, A, **kw):
+        """From an object with nrows, ncols, row_ptr, col, val, modulus."""
+        return cls(A.nrows, A.ncols, A.row_ptr, A.col, A.val, kw.pop("modulus", A.modulus), **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spmv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def describe(self):
+        return spmv_describe_plan(self.handle)
+
+    def info(self):
+        return spmv_get_info(self.handle)
+
+    def launches(self, transpose=False, nvec=1):
+        return spmv_count_launches(self.handle, transpose, nvec)
+
+    def _run(self, fn, x, y, out_rows, alpha, beta, stream):
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        x = _as_u32_tensor(x, dev)
+        nvec = 1 if x.dim() == 1 else x.shape[1]
+        if y is None:
+            shape = (out_rows,) if x.dim() == 1 else (out_rows, nvec)
+            y = torch.empty(shape, dtype=torch.int32, device=dev)
+            beta = 0
+        fn(self.handle, x, nvec, y, nvec, nvec, alpha, beta, stream)
+        return y
+
+    def apply(self, x, y=None, alpha=1, beta=0, stream=None):
+        """y <- alpha*A*x + beta*y (mod m); x: ncols or ncols x nvec."""
+        return self._run(spmv_apply, x, y, self.nrows, alpha, beta, stream)
+
+    def apply_transpose(self, x, y=None, alpha=1, beta=0, stream=None):
+        """y <- alpha*A^T*x + beta*y (mod m); x: nrows or nrows x nvec."""
+        return self._run(spmv_apply_transpose, x, y, self.ncols, alpha, beta, stream)
+
+    def block_sequence(self, X, Y, nsteps, want_next=False, stream=None):
+        """S_i = X^T A^i Y (mod m), 0 <= i < nsteps; X, Y: n x s."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        X = _as_u32_tensor(X, dev)
+        Y = _as_u32_tensor(Y, dev)
+        s = X.shape[1] if X.dim() == 2 else 1
+        S = torch.empty((max(int(nsteps), 0), s, s), dtype=torch.int32, device=dev)
+        Vn = torch.empty((self.nrows, s), dtype=torch.int32, device=dev) if want_next else None
+        spmv_block_sequence(self.handle, X, Y, s, nsteps, S, Vn, stream)
+        return (S, Vn) if want_next else S
+
+
+def to_numpy_u32(t):
+    """Host numpy uint32 copy of a 4-byte integer tensor."""
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+__all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
+           "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
+           "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "stream_ptr",
+           "to_numpy_u32",
+           "FFSPMVError", "Options"]

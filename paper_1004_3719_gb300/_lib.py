@@ -1,0 +1,118 @@
+"""ctypes declarations of the C ABI in include/ffspmv.h."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+
+class FFSPMVError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        msg = status_string(self.status) if _lib_handle is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {self.status})" if where else msg)
+
+
+class FMT:
+    AUTO, CSR, ELLR, COO, COOS, DIA, HYBRID, BINNED = range(8)
+
+
+class SEL:
+    HEURISTIC, LEARNED, EXHAUSTIVE, FIXED = range(4)
+
+
+class TRANSPOSE:
+    EXPLICIT, ATOMIC, NONE = range(3)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("selector", ctypes.c_int32),
+        ("use_pm1", ctypes.c_int32),
+        ("priority_format", ctypes.c_int32),
+        ("transpose_mode", ctypes.c_int32),
+        ("value_check", ctypes.c_int32),
+        ("group_width", ctypes.c_int32),
+        ("ell_width", ctypes.c_int32),
+        ("barrier_spin_limit", ctypes.c_uint32),
+        ("guard_bytes", ctypes.c_int64),
+        ("sequence_mode", ctypes.c_int32),
+        ("test_hooks", ctypes.c_int32),
+    ]
+
+
+_lib_handle = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_U32 = ctypes.c_uint32
+
+
+def _declare(L):
+    L.ffspmv_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.ffspmv_options_default.restype = None
+    L.ffspmv_status_string.argtypes = [ctypes.c_int]
+    L.ffspmv_status_string.restype = ctypes.c_char_p
+    L.spmv_create_hybrid.argtypes = [ctypes.POINTER(_P), _I64, _I64, _I64, _P, _P, _P,
+                                     _U32, ctypes.POINTER(Options), _P]
+    L.spmv_create_hybrid.restype = ctypes.c_int
+    for f in (L.spmv_apply, L.spmv_apply_transpose):
+        f.argtypes = [_P, _P, _I64, _P, _I64, _I32, _U32, _U32, _P]
+        f.restype = ctypes.c_int
+    L.spmv_block_sequence.argtypes = [_P, _P, _P, _I32, _I64, _P, _P, _P]
+    L.spmv_block_sequence.restype = ctypes.c_int
+    L.spmv_batch_apply.argtypes = [_I32, _P, _P, _P, _P, _P]
+    L.spmv_batch_apply.restype = ctypes.c_int
+    L.spmv_destroy.argtypes = [_P]
+    L.spmv_destroy.restype = ctypes.c_int
+    L.spmv_describe_plan.argtypes = [_P, ctypes.c_char_p, ctypes.c_size_t]
+    L.spmv_describe_plan.restype = ctypes.c_int
+    L.spmv_get_info.argtypes = [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                ctypes.POINTER(_I64), ctypes.POINTER(_U32),
+                                ctypes.POINTER(_I64)]
+    L.spmv_get_info.restype = ctypes.c_int
+    L.spmv_count_launches.argtypes = [_P, _I32, _I32, ctypes.POINTER(_I64)]
+    L.spmv_count_launches.restype = ctypes.c_int
+    for name, args, res in EXTRA_SIGNATURES:
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+
+
+# Entry points declared in include/ffspmv_select.h and include/ffspmv_batch.h.
+EXTRA_SIGNATURES = []
+
+
+def lib():
+    """The loaded CUDA library.  Raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        path = _build.OUT
+        if not os.path.exists(path):
+            raise FFSPMVError(4, f"{os.path.basename(path)} is not built "
+                              "(call paper_1004_3719_gb300.build())")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _lib_handle = L
+    return _lib_handle
+
+
+def status_string(s):
+    return lib().ffspmv_status_string(int(s)).decode()
+
+
+def check(status, where):
+    if status != 0:
+        raise FFSPMVError(status, where)
+
+
+def options_default(**kw):
+    o = Options()
+    lib().ffspmv_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o

@@ -1,0 +1,283 @@
+// The C ABI: argument checks, plan ownership, and dispatch to the kernels.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ff_internal.cuh"
+#include "ff_plan.h"
+#include "ff_select.h"
+
+using namespace ff;
+
+namespace {
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+ffspmv_status to_host(const T *p, long long n, std::vector<T> &out, const T *&view)
+{
+    if (n <= 0) {
+        view = p;
+        return FFSPMV_OK;
+    }
+    if (!is_device_ptr(p)) {
+        view = p;
+        return FFSPMV_OK;
+    }
+    out.resize((size_t)n);
+    FF_CUDA(cudaMemcpy(out.data(), p, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost));
+    view = out.data();
+    return FFSPMV_OK;
+}
+
+void destroy_handle(ffspmv_handle *h)
+{
+    if (!h) return;
+    free_plan(h->A);
+    free_plan(h->AT);
+    if (h->scatter) cudaFree(h->scatter);
+    if (h->csr_arena) cudaFree(h->csr_arena);
+    if (h->d_status) cudaFree(h->d_status);
+    free_sequence_state(h);
+    batch_forget(h);
+    delete h;
+}
+
+ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
+                                  const long long *ptr, const int *col,
+                                  const u32 *val, u32 m, const ffspmv_options &o)
+{
+    const bool wants_bins = o.priority_format == FFSPMV_FMT_BINNED ||
+                            (o.priority_format == FFSPMV_FMT_AUTO &&
+                             (o.selector == FFSPMV_SEL_LEARNED || o.selector == FFSPMV_SEL_EXHAUSTIVE));
+    if (wants_bins && (o.selector == FFSPMV_SEL_LEARNED || o.selector == FFSPMV_SEL_EXHAUSTIVE)) {
+        BinChoice bins[kBins];
+        ffspmv_status st = choose_bins(o.selector, nrows, ncols, ptr, col, val, m, o, bins);
+        if (st != FFSPMV_OK) return st;
+        ffspmv_options o2 = o;
+        o2.priority_format = FFSPMV_FMT_BINNED;
+        return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, bins);
+    }
+    ffspmv_options o2 = o;
+    if (o2.priority_format == FFSPMV_FMT_AUTO) o2.priority_format = FFSPMV_FMT_HYBRID;
+    return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ffspmv_options_default(ffspmv_options *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->selector = FFSPMV_SEL_HEURISTIC;
+    o->use_pm1 = -1;
+    o->priority_format = FFSPMV_FMT_AUTO;
+    o->transpose_mode = FFSPMV_TRANSPOSE_EXPLICIT;
+    o->value_check = 0;
+    o->group_width = 0;
+    o->ell_width = -1;
+    o->barrier_spin_limit = 0;
+    o->guard_bytes = 0;
+    o->sequence_mode = 0;
+    o->test_hooks = 0;
+}
+
+const char *ffspmv_status_string(ffspmv_status s)
+{
+    switch (s) {
+    case FFSPMV_OK: return "ok";
+    case FFSPMV_ERR_ARG: return "invalid argument";
+    case FFSPMV_ERR_RANGE: return "input residue out of range";
+    case FFSPMV_ERR_OOM: return "out of memory";
+    case FFSPMV_ERR_CUDA: return "CUDA runtime error";
+    case FFSPMV_ERR_UNSUPPORTED: return "unsupported format or size";
+    case FFSPMV_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
+                                 int64_t nnz, const int64_t *row_ptr,
+                                 const int32_t *col, const uint32_t *values,
+                                 uint32_t modulus, const ffspmv_options *opt,
+                                 ffspmv_stream_t stream)
+{
+    (void)stream;
+    if (!out) return FFSPMV_ERR_ARG;
+    *out = nullptr;
+    if (nrows < 0 || ncols < 0 || nnz < 0 || modulus < 2u || !row_ptr) return FFSPMV_ERR_ARG;
+    if (nrows >= (1LL << 32) - 1 || ncols >= (1LL << 31)) return FFSPMV_ERR_UNSUPPORTED;
+    if (nnz > 0 && (!col || !values)) return FFSPMV_ERR_ARG;
+    ffspmv_options o;
+    ffspmv_options_default(&o);
+    if (opt) o = *opt;
+    if (o.transpose_mode < 0 || o.transpose_mode > 2) return FFSPMV_ERR_ARG;
+
+    std::vector<long long> hptr;
+    std::vector<int> hcol;
+    std::vector<u32> hval;
+    const long long *ptr = nullptr;
+    const int *cidx = nullptr;
+    const u32 *vals = nullptr;
+    ffspmv_status st;
+    if ((st = to_host((const long long *)row_ptr, nrows + 1, hptr, ptr)) != FFSPMV_OK) return st;
+    if ((st = to_host((const int *)col, nnz, hcol, cidx)) != FFSPMV_OK) return st;
+    if ((st = to_host((const u32 *)values, nnz, hval, vals)) != FFSPMV_OK) return st;
+    if (ptr[0] != 0 || ptr[nrows] != nnz) return FFSPMV_ERR_ARG;
+    for (long long i = 0; i < nrows; ++i)
+        if (ptr[i + 1] < ptr[i]) return FFSPMV_ERR_ARG;
+    for (long long k = 0; k < nnz; ++k)
+        if (cidx[k] < 0 || cidx[k] >= ncols) return FFSPMV_ERR_ARG;
+
+    ffspmv_handle *h = new (std::nothrow) ffspmv_handle();
+    if (!h) return FFSPMV_ERR_OOM;
+    h->opt = o;
+    h->m = modulus;
+    h->transpose_mode = o.transpose_mode;
+    cudaGetDevice(&h->device);
+    if (cudaMalloc(&h->d_status, 4 * sizeof(int)) != cudaSuccess) {
+        h->d_status = nullptr;
+        destroy_handle(h);
+        return FFSPMV_ERR_OOM;
+    }
+    cudaMemset(h->d_status, 0, 4 * sizeof(int));
+    h->h_ptr.assign(ptr, ptr + nrows + 1);
+    h->h_col.assign(cidx, cidx + nnz);
+    h->h_val.resize((size_t)nnz);
+    for (long long k = 0; k < nnz; ++k) h->h_val[k] = vals[k] % modulus;
+    st = build_with_selector(h->A, nrows, ncols, ptr, cidx, vals, modulus, o);
+    if (st == FFSPMV_OK && o.transpose_mode == FFSPMV_TRANSPOSE_EXPLICIT) {
+        std::vector<long long> tptr;
+        std::vector<int> tcol;
+        std::vector<u32> tval;
+        transpose_csr(nrows, ncols, ptr, cidx, vals, tptr, tcol, tval);
+        st = build_with_selector(h->AT, ncols, nrows, tptr.data(), tcol.data(), tval.data(), modulus, o);
+        h->has_T = st == FFSPMV_OK;
+    }
+    if (st == FFSPMV_OK && o.transpose_mode == FFSPMV_TRANSPOSE_ATOMIC) {
+        size_t b_ptr = (size_t)(nrows + 1) * 8, b_col = (size_t)nnz * 4, b_val = (size_t)nnz * 4;
+        size_t o_col = (b_ptr + 255) / 256 * 256, o_val = o_col + (b_col + 255) / 256 * 256;
+        if (cudaMalloc(&h->csr_arena, o_val + b_val + 4) != cudaSuccess) {
+            h->csr_arena = nullptr;
+            st = FFSPMV_ERR_OOM;
+        } else {
+            std::vector<u32> red((size_t)nnz);
+            for (long long k = 0; k < nnz; ++k) red[k] = vals[k] % modulus;
+            char *base = (char *)h->csr_arena;
+            cudaMemcpy(base, ptr, b_ptr, cudaMemcpyHostToDevice);
+            if (nnz) {
+                cudaMemcpy(base + o_col, cidx, b_col, cudaMemcpyHostToDevice);
+                cudaMemcpy(base + o_val, red.data(), b_val, cudaMemcpyHostToDevice);
+            }
+            h->d_rowptr = (const long long *)base;
+            h->d_col = (const int *)(base + o_col);
+            h->d_val = (const u32 *)(base + o_val);
+            h->has_T = true;
+            if (cudaGetLastError() != cudaSuccess) st = FFSPMV_ERR_CUDA;
+        }
+    }
+    if (st != FFSPMV_OK) {
+        destroy_handle(h);
+        return st;
+    }
+    *out = h;
+    return FFSPMV_OK;
+}
+
+static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_x,
+                                  int64_t ldx, uint32_t *d_y, int64_t ldy,
+                                  int32_t nvec, uint32_t alpha, uint32_t beta,
+                                  ffspmv_stream_t stream)
+{
+    if (!h || nvec < 1 || ldx < nvec || ldy < nvec) return FFSPMV_ERR_ARG;
+    const long long in_rows = transpose ? h->A.nrows : h->A.ncols;
+    const long long out_rows = transpose ? h->A.ncols : h->A.nrows;
+    if ((in_rows > 0 && !d_x) || (out_rows > 0 && !d_y)) return FFSPMV_ERR_ARG;
+    if (transpose && !h->has_T) return FFSPMV_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->opt.value_check) {
+        bool bad = false;
+        ffspmv_status s = check_range(d_x, in_rows, ldx, nvec, h->m, h->d_status + 1, st, &bad);
+        if (s != FFSPMV_OK) return s;
+        if (bad) return FFSPMV_ERR_RANGE;
+    }
+    if (out_rows == 0) return FFSPMV_OK;
+    if (transpose && h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC)
+        return run_scatter_transpose(h, d_x, ldx, d_y, ldy, nvec, alpha % h->m, beta % h->m, st);
+    const Plan &P = transpose ? h->AT : h->A;
+    return run_plan(P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st);
+}
+
+ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx, uint32_t *d_y,
+                         int64_t ldy, int32_t nvec, uint32_t alpha, uint32_t beta,
+                         ffspmv_stream_t stream)
+{
+    return apply_common(h, false, d_x, ldx, d_y, ldy, nvec, alpha, beta, stream);
+}
+
+ffspmv_status spmv_apply_transpose(ffspmv_t h, const uint32_t *d_x, int64_t ldx,
+                                   uint32_t *d_y, int64_t ldy, int32_t nvec,
+                                   uint32_t alpha, uint32_t beta, ffspmv_stream_t stream)
+{
+    return apply_common(h, true, d_x, ldx, d_y, ldy, nvec, alpha, beta, stream);
+}
+
+ffspmv_status spmv_destroy(ffspmv_t h)
+{
+    destroy_handle(h);
+    return FFSPMV_OK;
+}
+
+ffspmv_status spmv_describe_plan(ffspmv_t h, char *buf, size_t len)
+{
+    if (!h || !buf || len == 0) return FFSPMV_ERR_ARG;
+    std::string s = "A  " + h->A.summary;
+    if (h->has_T && h->transpose_mode == FFSPMV_TRANSPOSE_EXPLICIT) s += "A^T " + h->AT.summary;
+    else if (h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC) s += "A^T by 64-bit atomic scatter\n";
+    size_t n = s.size() < len - 1 ? s.size() : len - 1;
+    memcpy(buf, s.data(), n);
+    buf[n] = '\0';
+    return FFSPMV_OK;
+}
+
+ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec, int64_t *launches)
+{
+    if (!h || !launches || nvec < 1) return FFSPMV_ERR_ARG;
+    long long n = 0;
+    if (transpose && !h->has_T) return FFSPMV_ERR_UNSUPPORTED;
+    if (h->opt.value_check) n += 1;
+    if (transpose && h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC) {
+        const int chunk = nvec < 16 ? nvec : 16;
+        n += 2LL * ((nvec + chunk - 1) / chunk);
+    } else {
+        n += count_plan_launches(transpose ? h->AT : h->A, nvec);
+    }
+    *launches = n;
+    return FFSPMV_OK;
+}
+
+ffspmv_status spmv_get_info(ffspmv_t h, int64_t *nrows, int64_t *ncols, int64_t *nnz,
+                            uint32_t *modulus, int64_t *device_bytes)
+{
+    if (!h) return FFSPMV_ERR_ARG;
+    if (nrows) *nrows = h->A.nrows;
+    if (ncols) *ncols = h->A.ncols;
+    if (nnz) *nnz = h->A.nnz;
+    if (modulus) *modulus = h->m;
+    if (device_bytes)
+        *device_bytes = (int64_t)(h->A.arena_bytes + h->AT.arena_bytes);
+    return FFSPMV_OK;
+}
+
+}  // extern "C"

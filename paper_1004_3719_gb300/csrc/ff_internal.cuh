@@ -1,0 +1,236 @@
+// Internal definitions shared by the CUDA translation units of libffspmv.
+//
+// Residue arithmetic (Sec. 2.2): sums of products are formed exactly in
+// integer accumulators and reduced once per output.  The reduction is
+// Barrett's (P. Barrett, "Implementing the Rivest Shamir and Adleman public
+// key encryption algorithm on a standard digital signal processor", CRYPTO
+// 1986) with the 64-bit reciprocal mu = floor(2^64 / m).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ffspmv.h"
+
+namespace ff {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ---------------------------------------------------------------------------
+// Modulus parameters.
+struct Mod {
+    u32 m;      // modulus, 2 <= m <= 2^32 - 1
+    u32 c64;    // 2^64 mod m
+    u64 mu;     // floor(2^64 / m)
+    u32 alpha;  // < m
+    u32 beta;   // < m
+};
+
+Mod make_mod(u32 m, u32 alpha, u32 beta);  // host
+
+// x mod m for any 64-bit x.  With mu = floor(2^64/m), q = floor(x*mu/2^64)
+// lies in {floor(x/m) - 1, floor(x/m)}, so one conditional subtraction ends
+// in [0, m).
+__device__ __forceinline__ u32 red64(u64 x, const Mod &M)
+{
+    u64 q = __umul64hi(x, M.mu);
+    u64 r = x - q * (u64)M.m;
+    if (r >= M.m) r -= M.m;
+    return (u32)r;
+}
+
+__device__ __forceinline__ u32 addmod(u32 a, u32 b, u32 m)
+{
+    u64 s = (u64)a + b;
+    return (u32)(s >= m ? s - m : s);
+}
+
+// y_new = alpha*r + beta*y_old (first writer of a row) or y_old + alpha*r
+// (a later part adding into the same row).  r < m.
+__device__ __forceinline__ u32 combine(u32 r, const u32 *yp, bool accum,
+                                       const Mod &M)
+{
+    u32 a = (M.alpha == 1u) ? r : red64((u64)M.alpha * r, M);
+    if (accum) return addmod(*yp, a, M.m);
+    if (M.beta == 0u) return a;
+    u32 b = (M.beta == 1u) ? *yp : red64((u64)M.beta * (*yp), M);
+    return addmod(a, b, M.m);
+}
+
+// ---------------------------------------------------------------------------
+// Accumulators.  AccSmall is one 64-bit word and is used when the plan has
+// checked that no output sums more than floor((2^64-1)/B) terms, B the
+// largest term (Sec. 2.2's M/m^2 bound with M = 2^64 - 1); AccWide carries
+// into a third 32-bit word and never overflows for rows below 2^34 entries.
+struct AccSmall {
+    u64 v;
+    __device__ __forceinline__ void zero() { v = 0; }
+    __device__ __forceinline__ void mad(u32 a, u32 b) { v += (u64)a * b; }
+    __device__ __forceinline__ void add(u32 a) { v += a; }
+    // a 64-bit value congruent to the sum; group sums of these stay exact
+    __device__ __forceinline__ u64 partial(const Mod &) const { return v; }
+};
+
+struct AccWide {
+    u32 w0, w1, w2;
+    __device__ __forceinline__ void zero() { w0 = w1 = w2 = 0; }
+    __device__ __forceinline__ void mad(u32 a, u32 b)
+    {
+        asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+            "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+r"(w0), "+r"(w1), "+r"(w2)
+            : "r"(a), "r"(b));
+    }
+    __device__ __forceinline__ void add(u32 a)
+    {
+        asm("add.cc.u32 %0, %0, %3;\n\t"
+            "addc.cc.u32 %1, %1, 0;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+r"(w0), "+r"(w1), "+r"(w2)
+            : "r"(a));
+    }
+    // (w2*2^64 + w1*2^32 + w0) mod m, a value below m
+    __device__ __forceinline__ u64 partial(const Mod &M) const
+    {
+        u32 lo = red64(((u64)w1 << 32) | w0, M);
+        u32 hi = red64((u64)w2 * M.c64, M);
+        return addmod(lo, hi, M.m);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Plan segments.  A plan is a list of segments; each covers a set of rows
+// (or of entries, for COO) in one storage format.  Segments of one phase own
+// disjoint rows and run in one launch; phase 2 segments add into rows that a
+// phase 1 segment has already written (the column split of Sec. 2.4.5).
+enum SegKind : int {
+    SEG_CSR = 0,     // `group` lanes per row
+    SEG_CSRBLK = 1,  // one CTA per row
+    SEG_ELLR = 2,    // one thread per row: DIA diagonals + ELL_R columns
+    SEG_COO = 3,     // element-parallel segmented sums over sorted entries
+    SEG_EMPTY = 4    // rows with no entry: y <- beta*y
+};
+
+constexpr int kThreads = 256;        // threads per CTA for every plan kernel
+constexpr int kCooRuns = 8;          // 32-entry runs per warp chunk (COO)
+constexpr u32 kClassShift = 30;      // +-1 class in the top two bits of col
+constexpr u32 kColMask = (1u << kClassShift) - 1u;
+constexpr u32 kPlus = 1u, kMinus = 2u;
+constexpr int kMaxSeg = 24;
+
+struct SegDesc {
+    int kind;
+    int accum;       // 0: first writer (applies beta), 1: adds into y
+    int group;       // CSR lanes per row (power of two, 1..32)
+    int vbytes;      // bytes per stored value: 0 (all +-1), 2 or 4
+    int pm;          // column words carry the +-1 class bits
+    int ndiag;       // DIA diagonals (SEG_ELLR)
+    int width;       // ELL_R columns (SEG_ELLR)
+    int dvbytes;     // bytes per DIA value: 2 or 4
+    long long nrows;     // rows in the segment (SEG_COO: rows spanned)
+    long long nnz;       // entries in the segment
+    long long row0;      // first row when `rows` is NULL
+    long long ld;        // ELL_R / DIA leading dimension (>= nrows)
+    long long block0;    // first CTA of this segment in its launch
+    long long nblocks;
+    const u32 *rows;     // local row -> matrix row, or NULL (row0 + local)
+    const u32 *ptr;      // CSR: local offsets, nrows + 1
+    const u32 *vptr;     // CSR with +-1 and values: value offsets, nrows + 1
+    const u32 *col;      // column words
+    const void *val;     // u16 or u32 values
+    const u32 *rowid;    // COO: matrix row of each entry (sorted)
+    const u32 *rownb;    // ELL_R: entries per row
+    const int *doff;     // DIA offsets (column - row)
+    const void *dval;    // DIA values [ndiag][ld]
+    long long ncols;     // columns of the matrix (DIA bounds)
+};
+
+struct PlanParams {
+    int nseg;
+    int acc_wide;
+    long long total_blocks;
+    SegDesc seg[kMaxSeg];
+};
+
+struct Phase {
+    std::vector<SegDesc> segs;
+    std::vector<u32> split_rows_host;  // COO rows shared between warp chunks
+    const u32 *split_rows = nullptr;   // device copy
+    long long nsplit = 0;
+    bool has_coo = false;
+};
+
+// One matrix plan (A or A^T).
+struct Plan {
+    long long nrows = 0, ncols = 0, nnz = 0;
+    int acc_wide = 0;
+    int format = 0;
+    std::vector<Phase> phases;  // 1 or 2
+    void *arena = nullptr;      // one device allocation for all parts
+    size_t arena_bytes = 0;
+    u64 *carry = nullptr;       // COO carries, zero between calls (nrows)
+    std::string summary;
+    long long max_row = 0;
+    double pm_fraction = 0.0;
+};
+
+}  // namespace ff
+
+struct ffspmv_handle {
+    ff::Plan A;
+    ff::Plan AT;
+    bool has_T = false;
+    int transpose_mode = 0;
+    ffspmv_options opt;
+    uint32_t m = 0;
+    int device = 0;
+    // transpose by atomics: exact 64-bit sums per column
+    ff::u64 *scatter = nullptr;
+    size_t scatter_elems = 0;
+    // host copy of the CSR for the atomic transpose (device arrays)
+    void *csr_arena = nullptr;
+    const long long *d_rowptr = nullptr;
+    const int *d_col = nullptr;
+    const ff::u32 *d_val = nullptr;
+    // host copy of the CSR (values reduced mod m), for layouts built later
+    std::vector<long long> h_ptr;
+    std::vector<int> h_col;
+    std::vector<ff::u32> h_val;
+    // block sequence state
+    void *seq_state = nullptr;
+    int *d_status = nullptr;   // device status word (timeouts)
+};
+
+namespace ff {
+
+// plan.cu
+ffspmv_status build_plan(Plan &P, long long nrows, long long ncols,
+                         const long long *ptr, const int *col, const u32 *val,
+                         u32 m, const ffspmv_options &opt, cudaStream_t st);
+void free_plan(Plan &P);
+
+// kernels.cu
+ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
+                       long long ldy, int nvec, u32 m, u32 alpha, u32 beta,
+                       cudaStream_t st);
+ffspmv_status run_scatter_transpose(ffspmv_handle *h, const u32 *x,
+                                    long long ldx, u32 *y, long long ldy,
+                                    int nvec, u32 alpha, u32 beta,
+                                    cudaStream_t st);
+long long count_plan_launches(const Plan &P, int nvec);
+ffspmv_status check_range(const u32 *x, long long rows, long long ld,
+                          int nvec, u32 m, int *d_flag, cudaStream_t st,
+                          bool *bad);
+
+}  // namespace ff
+
+#define FF_CUDA(call)                                            \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return FFSPMV_ERR_CUDA;           \
+    } while (0)

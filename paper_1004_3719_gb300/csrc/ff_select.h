@@ -1,0 +1,18 @@
+// Format selection (exhaustive search, selector network) and the block
+// sequence state, shared between host translation units.
+#pragma once
+
+#include "ff_plan.h"
+
+namespace ff {
+
+// Pick one format per row bin with `selector` (FFSPMV_SEL_LEARNED or
+// FFSPMV_SEL_EXHAUSTIVE).  bins[kBins] receives the choice.
+ffspmv_status choose_bins(int selector, long long nrows, long long ncols,
+                          const long long *ptr, const int *col, const u32 *val,
+                          u32 m, const ffspmv_options &o, BinChoice *bins);
+
+void free_sequence_state(ffspmv_handle *h);
+void batch_forget(ffspmv_handle *h);
+
+}  // namespace ff

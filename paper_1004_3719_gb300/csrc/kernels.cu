@@ -1,0 +1,552 @@
+// SpMV / SpMM kernels over Z/mZ for every plan segment format.
+//
+// One launch runs every segment of a plan phase: CTA b belongs to the segment
+// whose CTA range holds b, and runs that segment's device routine.  Each
+// routine forms the exact sums of Sec. 2 (y <- alpha*A*x + beta*y, block form
+// with NV vectors per launch) in integer accumulators and reduces once per
+// output (Sec. 2.2, delayed reduction); +-1 entries flagged in the column
+// word add or subtract x instead of multiplying (Sec. 2.4.2).
+#include "ff_internal.cuh"
+
+namespace ff {
+
+Mod make_mod(u32 m, u32 alpha, u32 beta)
+{
+    Mod M;
+    unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    M.m = m;
+    M.mu = (u64)(two64 / m);
+    M.c64 = (u32)(two64 % m);
+    M.alpha = alpha % m;
+    M.beta = beta % m;
+    return M;
+}
+
+__device__ __forceinline__ u32 load_val(const void *p, long long i, int vbytes)
+{
+    if (vbytes == 2) return __ldg(reinterpret_cast<const unsigned short *>(p) + i);
+    return __ldg(reinterpret_cast<const u32 *>(p) + i);
+}
+
+template <int NV>
+__device__ __forceinline__ void load_x(const u32 *__restrict__ x, long long j,
+                                       long long ldx, u32 (&xv)[NV], bool vec4)
+{
+    const u32 *p = x + j * ldx;
+    if constexpr (NV >= 4) {
+        if (vec4) {
+#pragma unroll
+            for (int i = 0; i < NV / 4; ++i) {
+                uint4 t = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+                xv[4 * i + 0] = t.x;
+                xv[4 * i + 1] = t.y;
+                xv[4 * i + 2] = t.z;
+                xv[4 * i + 3] = t.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xv[v] = __ldg(p + v);
+}
+
+template <int NV, class Acc>
+__device__ __forceinline__ void apply_entry(Acc (&acc)[NV], u32 cls, u32 val,
+                                            const u32 (&xv)[NV], u32 m)
+{
+    if (cls == 0u) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v].mad(val, xv[v]);
+    } else if (cls == kPlus) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v].add(xv[v]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v].add(m - xv[v]);
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void write_row(u32 *__restrict__ y, long long row,
+                                          long long ldy, const u64 (&part)[NV],
+                                          bool accum, const Mod &M)
+{
+    u32 *yp = y + row * ldy;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) yp[v] = combine(red64(part[v], M), yp + v, accum, M);
+}
+
+// ---------------------------------------------------------------------------
+// CSR, `group` lanes per row (a power of two up to 32).
+template <class Acc, int NV>
+__device__ void seg_csr(const SegDesc &S, long long lb, const u32 *__restrict__ x,
+                        long long ldx, u32 *__restrict__ y, long long ldy,
+                        const Mod &M, bool vec4)
+{
+    const int G = S.group;
+    const int gid = threadIdx.x / G;
+    const int lane = threadIdx.x & (G - 1);
+    const long long r = lb * (kThreads / G) + gid;
+    const bool active = r < S.nrows;
+    Acc acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v].zero();
+    if (active) {
+        const u32 start = __ldg(S.ptr + r), end = __ldg(S.ptr + r + 1);
+        const u32 vbase = S.vptr ? __ldg(S.vptr + r) : start;
+        for (u32 k = start + lane; k < end; k += G) {
+            u32 c = __ldg(S.col + k);
+            u32 cls = 0;
+            if (S.pm) {
+                cls = c >> kClassShift;
+                c &= kColMask;
+            }
+            u32 a = (cls == 0u) ? load_val(S.val, (long long)vbase + (k - start), S.vbytes) : 0u;
+            u32 xv[NV];
+            load_x<NV>(x, c, ldx, xv, vec4);
+            apply_entry<NV>(acc, cls, a, xv, M.m);
+        }
+    }
+    u64 part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v] = acc[v].partial(M);
+    for (int off = G >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
+    }
+    if (active && lane == 0) {
+        const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
+        write_row<NV>(y, row, ldy, part, S.accum, M);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CSR, one CTA per row (long rows).
+template <class Acc, int NV>
+__device__ void seg_csrblk(const SegDesc &S, long long lb, const u32 *__restrict__ x,
+                           long long ldx, u32 *__restrict__ y, long long ldy,
+                           const Mod &M, bool vec4)
+{
+    __shared__ u64 red[kThreads / 32][NV];
+    const long long r = lb;
+    const u32 start = __ldg(S.ptr + r), end = __ldg(S.ptr + r + 1);
+    const u32 vbase = S.vptr ? __ldg(S.vptr + r) : start;
+    Acc acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v].zero();
+    for (u32 k = start + threadIdx.x; k < end; k += kThreads) {
+        u32 c = __ldg(S.col + k);
+        u32 cls = 0;
+        if (S.pm) {
+            cls = c >> kClassShift;
+            c &= kColMask;
+        }
+        u32 a = (cls == 0u) ? load_val(S.val, (long long)vbase + (k - start), S.vbytes) : 0u;
+        u32 xv[NV];
+        load_x<NV>(x, c, ldx, xv, vec4);
+        apply_entry<NV>(acc, cls, a, xv, M.m);
+    }
+    u64 part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v] = acc[v].partial(M);
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red[w][v] = part[v];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            u64 s = 0;
+            for (int i = 0; i < kThreads / 32; ++i) s += red[i][v];
+            part[v] = s;
+        }
+        const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
+        write_row<NV>(y, row, ldy, part, S.accum, M);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One thread per row: DIA diagonals, then ELL_R columns (column-major, Sec.
+// 2.1; coalesced on the GPU, Sec. 2.4.4).
+template <class Acc, int NV>
+__device__ void seg_ellr(const SegDesc &S, long long lb, const u32 *__restrict__ x,
+                         long long ldx, u32 *__restrict__ y, long long ldy,
+                         const Mod &M, bool vec4)
+{
+    const long long r = lb * kThreads + threadIdx.x;
+    if (r >= S.nrows) return;
+    const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
+    Acc acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v].zero();
+    for (int d = 0; d < S.ndiag; ++d) {
+        const long long j = row + __ldg(S.doff + d);
+        if (j >= 0 && j < S.ncols) {
+            u32 a = load_val(S.dval, (long long)d * S.ld + r, S.dvbytes);
+            u32 xv[NV];
+            load_x<NV>(x, j, ldx, xv, vec4);
+            apply_entry<NV>(acc, 0u, a, xv, M.m);
+        }
+    }
+    const int n = S.rownb ? (int)__ldg(S.rownb + r) : S.width;
+    for (int j = 0; j < n; ++j) {
+        const long long idx = (long long)j * S.ld + r;
+        u32 c = __ldg(S.col + idx);
+        u32 cls = 0;
+        if (S.pm) {
+            cls = c >> kClassShift;
+            c &= kColMask;
+        }
+        u32 a = (cls == 0u) ? load_val(S.val, idx, S.vbytes) : 0u;
+        u32 xv[NV];
+        load_x<NV>(x, c, ldx, xv, vec4);
+        apply_entry<NV>(acc, cls, a, xv, M.m);
+    }
+    u64 part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v] = acc[v].partial(M);
+    write_row<NV>(y, row, ldy, part, S.accum, M);
+}
+
+// ---------------------------------------------------------------------------
+// COO: each warp owns 32*kCooRuns consecutive entries (sorted by row) and
+// forms per-row sums by a segmented warp scan of reduced terms.  A row that
+// also has entries in another warp's chunk adds its partial sum into
+// `carry[row]` with an exact 64-bit atomic; a second launch finishes those
+// rows.  One vector per launch.
+__device__ __forceinline__ u64 coo_term(u32 cls, u32 a, u32 xv, const Mod &M)
+{
+    if (cls == 0u) return red64((u64)a * xv, M);
+    if (cls == kPlus) return xv;
+    return (u64)(M.m - xv);
+}
+
+__device__ void seg_coo(const SegDesc &S, long long lb, const u32 *__restrict__ x,
+                        long long ldx, u32 *__restrict__ y, long long ldy,
+                        const Mod &M, u64 *__restrict__ carry)
+{
+    const int lane = threadIdx.x & 31;
+    const long long w = lb * (kThreads / 32) + (threadIdx.x >> 5);
+    const long long cb = w * (32LL * kCooRuns);
+    if (cb >= S.nnz) return;
+    const long long ce = min(S.nnz, cb + 32LL * kCooRuns);
+    const u32 first_row = __ldg(S.rowid + cb);
+    const u32 last_row = __ldg(S.rowid + ce - 1);
+    const bool started_before = cb > 0 && __ldg(S.rowid + cb - 1) == first_row;
+    const bool continues_after = ce < S.nnz && __ldg(S.rowid + ce) == last_row;
+    const u32 kNone = 0xffffffffu;
+
+    u32 carry_row = kNone;
+    u64 carry_val = 0;
+
+    auto flush = [&](u32 row, u64 s) {
+        const bool shared_row = (row == first_row && started_before) ||
+                                (row == last_row && continues_after);
+        if (shared_row) {
+            atomicAdd(carry + row, (u64)red64(s, M));
+        } else {
+            u32 *yp = y + (long long)row * ldy;
+            *yp = combine(red64(s, M), yp, S.accum, M);
+        }
+    };
+
+    for (long long base = cb; base < ce; base += 32) {
+        const long long k = base + lane;
+        const bool valid = k < ce;
+        u32 row = kNone, cls = 0, a = 0, xv = 0;
+        if (valid) {
+            row = __ldg(S.rowid + k);
+            u32 c = __ldg(S.col + k);
+            if (S.pm) {
+                cls = c >> kClassShift;
+                c &= kColMask;
+            }
+            if (cls == 0u) a = load_val(S.val, k, S.vbytes);
+            xv = __ldg(x + (long long)c * ldx);
+        }
+        // the run carried from the previous 32 entries ends here unless
+        // this run starts with the same row
+        const u32 r0 = __shfl_sync(0xffffffffu, row, 0);
+        if (carry_row != kNone && r0 != carry_row) {
+            if (lane == 0) flush(carry_row, carry_val);
+            carry_row = kNone;
+            carry_val = 0;
+        }
+        u32 prev = __shfl_up_sync(0xffffffffu, row, 1);
+        if (lane == 0) prev = carry_row;
+        u32 next = __shfl_down_sync(0xffffffffu, row, 1);
+        const bool tail = valid && (lane == 31 || row != next);
+        u64 s = valid ? coo_term(cls, a, xv, M) : 0;
+        if (lane == 0 && valid && row == carry_row) s += carry_val;
+        bool head = !valid || row != prev;
+        // segmented inclusive scan (heads stop the sum)
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            u64 o = __shfl_up_sync(0xffffffffu, s, off);
+            int ho = __shfl_up_sync(0xffffffffu, (int)head, off);
+            if (lane >= off) {
+                if (!head) s += o;
+                head = head || ho;
+            }
+        }
+        const bool lane31_valid = __shfl_sync(0xffffffffu, (int)valid, 31);
+        if (tail && lane != 31) flush(row, s);
+        if (lane31_valid) {
+            carry_row = __shfl_sync(0xffffffffu, row, 31);
+            u64 cv = __shfl_sync(0xffffffffu, s, 31);
+            carry_val = red64(cv, M);
+        } else {
+            carry_row = kNone;
+            carry_val = 0;
+        }
+    }
+    if (lane == 0 && carry_row != kNone) flush(carry_row, carry_val);
+}
+
+// ---------------------------------------------------------------------------
+// Rows without entries: y <- beta*y (first writer only).
+template <int NV>
+__device__ void seg_empty(const SegDesc &S, long long lb, u32 *__restrict__ y,
+                          long long ldy, const Mod &M)
+{
+    const long long r = lb * kThreads + threadIdx.x;
+    if (r >= S.nrows || S.accum) return;
+    const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
+    u32 *yp = y + row * ldy;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        yp[v] = (M.beta == 0u) ? 0u : red64((u64)M.beta * yp[v], M);
+}
+
+template <class Acc, int NV>
+__global__ void __launch_bounds__(kThreads)
+k_plan(const __grid_constant__ PlanParams P, const u32 *__restrict__ x,
+       long long ldx, u32 *__restrict__ y, long long ldy, const Mod M,
+       u64 *__restrict__ carry, int vec4)
+{
+    const long long b = blockIdx.x;
+    int s = 0;
+    while (s + 1 < P.nseg && b >= P.seg[s + 1].block0) ++s;
+    const SegDesc &S = P.seg[s];
+    const long long lb = b - S.block0;
+    switch (S.kind) {
+    case SEG_CSR: seg_csr<Acc, NV>(S, lb, x, ldx, y, ldy, M, vec4 != 0); break;
+    case SEG_CSRBLK: seg_csrblk<Acc, NV>(S, lb, x, ldx, y, ldy, M, vec4 != 0); break;
+    case SEG_ELLR: seg_ellr<Acc, NV>(S, lb, x, ldx, y, ldy, M, vec4 != 0); break;
+    case SEG_COO:
+        if constexpr (NV == 1) seg_coo(S, lb, x, ldx, y, ldy, M, carry);
+        break;
+    case SEG_EMPTY: seg_empty<NV>(S, lb, y, ldy, M); break;
+    default: break;
+    }
+}
+
+// Rows whose COO entries spanned several warp chunks.
+__global__ void k_coo_finish(const u32 *__restrict__ rows, long long n,
+                             u64 *__restrict__ carry, u32 *__restrict__ y,
+                             long long ldy, const Mod M, int accum)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u32 row = rows[i];
+    const u64 c = carry[row];
+    carry[row] = 0;
+    u32 *yp = y + (long long)row * ldy;
+    *yp = combine(red64(c, M), yp, accum != 0, M);
+}
+
+template <class Acc, int NV>
+static void launch_phase(const PlanParams &pp, const u32 *x, long long ldx,
+                         u32 *y, long long ldy, const Mod &M, u64 *carry,
+                         bool vec4, cudaStream_t st)
+{
+    k_plan<Acc, NV><<<(unsigned)pp.total_blocks, kThreads, 0, st>>>(
+        pp, x, ldx, y, ldy, M, carry, vec4 ? 1 : 0);
+}
+
+template <class Acc>
+static void launch_nv(int nv, const PlanParams &pp, const u32 *x, long long ldx,
+                      u32 *y, long long ldy, const Mod &M, u64 *carry,
+                      bool vec4, cudaStream_t st)
+{
+    switch (nv) {
+    case 16: launch_phase<Acc, 16>(pp, x, ldx, y, ldy, M, carry, vec4, st); break;
+    case 8: launch_phase<Acc, 8>(pp, x, ldx, y, ldy, M, carry, vec4, st); break;
+    case 4: launch_phase<Acc, 4>(pp, x, ldx, y, ldy, M, carry, vec4, st); break;
+    case 2: launch_phase<Acc, 2>(pp, x, ldx, y, ldy, M, carry, vec4, st); break;
+    default: launch_phase<Acc, 1>(pp, x, ldx, y, ldy, M, carry, vec4, st); break;
+    }
+}
+
+static PlanParams params_of(const Phase &ph, int acc_wide)
+{
+    PlanParams pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.nseg = (int)ph.segs.size();
+    pp.acc_wide = acc_wide;
+    long long total = 0;
+    for (int i = 0; i < pp.nseg; ++i) {
+        pp.seg[i] = ph.segs[i];
+        total = pp.seg[i].block0 + pp.seg[i].nblocks;
+    }
+    pp.total_blocks = total;
+    return pp;
+}
+
+static int next_chunk(int left, bool has_coo)
+{
+    if (has_coo) return 1;
+    return left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+}
+
+long long count_plan_launches(const Plan &P, int nvec)
+{
+    if (P.nrows == 0) return 0;
+    long long n = 0;
+    for (const Phase &ph : P.phases) {
+        if (ph.segs.empty()) continue;
+        for (int c0 = 0; c0 < nvec; c0 += next_chunk(nvec - c0, ph.has_coo))
+            n += 1 + (ph.nsplit > 0 ? 1 : 0);
+    }
+    return n;
+}
+
+ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
+                       long long ldy, int nvec, u32 m, u32 alpha, u32 beta,
+                       cudaStream_t st)
+{
+    const Mod M1 = make_mod(m, alpha, beta);
+    for (size_t pi = 0; pi < P.phases.size(); ++pi) {
+        const Phase &ph = P.phases[pi];
+        if (ph.segs.empty()) continue;
+        PlanParams pp = params_of(ph, P.acc_wide);
+        if (pp.total_blocks <= 0) continue;
+        int c0 = 0;
+        while (c0 < nvec) {
+            int nv = next_chunk(nvec - c0, ph.has_coo);
+            const u32 *xc = x + c0;
+            u32 *yc = y + c0;
+            bool vec4 = nv >= 4 && (ldx % 4 == 0) && ((uintptr_t)xc % 16 == 0);
+            if (P.acc_wide)
+                launch_nv<AccWide>(nv, pp, xc, ldx, yc, ldy, M1, P.carry, vec4, st);
+            else
+                launch_nv<AccSmall>(nv, pp, xc, ldx, yc, ldy, M1, P.carry, vec4, st);
+            FF_CUDA(cudaGetLastError());
+            if (ph.nsplit > 0) {
+                int accum = ph.segs[0].accum;
+                unsigned nb = (unsigned)((ph.nsplit + 255) / 256);
+                k_coo_finish<<<nb, 256, 0, st>>>(ph.split_rows, ph.nsplit, P.carry, yc, ldy, M1, accum);
+                FF_CUDA(cudaGetLastError());
+            }
+            c0 += nv;
+        }
+    }
+    return FFSPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A^T * x by scatter: every entry adds its reduced term into the exact 64-bit
+// column sum acc[j*nv + v] (integer atomics are order independent, so the
+// result is the same as the explicit transposed plan's).
+__global__ void k_scatter_T(long long nrows, const long long *__restrict__ ptr,
+                            const int *__restrict__ col, const u32 *__restrict__ val,
+                            const u32 *__restrict__ x, long long ldx, int nv,
+                            u64 *__restrict__ acc, const Mod M)
+{
+    const int G = 8;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x & (G - 1);
+    if (i >= nrows) return;
+    const long long s = ptr[i], e = ptr[i + 1];
+    for (long long k = s + lane; k < e; k += G) {
+        const long long j = col[k];
+        const u32 a = val[k];
+        for (int v = 0; v < nv; ++v) {
+            u32 t = red64((u64)a * __ldg(x + i * ldx + v), M);
+            if (t) atomicAdd(acc + j * nv + v, (u64)t);
+        }
+    }
+}
+
+__global__ void k_scatter_finish(long long ncols, int nv, u64 *__restrict__ acc,
+                                 u32 *__restrict__ y, long long ldy, const Mod M)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncols * nv) return;
+    const long long j = t / nv;
+    const int v = (int)(t - j * nv);
+    const u64 c = acc[t];
+    acc[t] = 0;
+    u32 *yp = y + j * ldy + v;
+    *yp = combine(red64(c, M), yp, false, M);
+}
+
+ffspmv_status run_scatter_transpose(ffspmv_handle *h, const u32 *x,
+                                    long long ldx, u32 *y, long long ldy,
+                                    int nvec, u32 alpha, u32 beta,
+                                    cudaStream_t st)
+{
+    const long long nrows = h->A.nrows, ncols = h->A.ncols;
+    const Mod M = make_mod(h->m, alpha, beta);
+    const int chunk = nvec < 16 ? nvec : 16;
+    size_t need = (size_t)(ncols > 0 ? ncols : 1) * chunk;
+    if (need > h->scatter_elems) {
+        if (h->scatter) cudaFree(h->scatter);
+        h->scatter = nullptr;
+        h->scatter_elems = 0;
+        if (cudaMalloc(&h->scatter, need * sizeof(u64)) != cudaSuccess) return FFSPMV_ERR_OOM;
+        if (cudaMemset(h->scatter, 0, need * sizeof(u64)) != cudaSuccess) return FFSPMV_ERR_CUDA;
+        h->scatter_elems = need;
+    }
+    for (int c0 = 0; c0 < nvec; c0 += chunk) {
+        int nv = nvec - c0 < chunk ? nvec - c0 : chunk;
+        if (nrows > 0) {
+            long long threads = nrows * 8;
+            unsigned nb = (unsigned)((threads + 255) / 256);
+            k_scatter_T<<<nb, 256, 0, st>>>(nrows, h->d_rowptr, h->d_col, h->d_val,
+                                            x + c0, ldx, nv, h->scatter, M);
+            FF_CUDA(cudaGetLastError());
+        }
+        if (ncols > 0) {
+            long long t = ncols * nv;
+            k_scatter_finish<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(ncols, nv, h->scatter, y + c0, ldy, M);
+            FF_CUDA(cudaGetLastError());
+        }
+    }
+    return FFSPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_check_range(const u32 *__restrict__ x, long long rows,
+                              long long ld, int nvec, u32 m, int *flag)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * nvec) return;
+    const long long r = t / nvec;
+    const int v = (int)(t - r * nvec);
+    if (x[r * ld + v] >= m) atomicExch(flag, 1);
+}
+
+ffspmv_status check_range(const u32 *x, long long rows, long long ld, int nvec,
+                          u32 m, int *d_flag, cudaStream_t st, bool *bad)
+{
+    *bad = false;
+    if (rows == 0) return FFSPMV_OK;
+    FF_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+    long long t = rows * nvec;
+    k_check_range<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(x, rows, ld, nvec, m, d_flag);
+    FF_CUDA(cudaGetLastError());
+    int hflag = 0;
+    FF_CUDA(cudaMemcpyAsync(&hflag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaStreamSynchronize(st));
+    *bad = hflag != 0;
+    return FFSPMV_OK;
+}
+
+}  // namespace ff

@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every entry point that include/*.h declares; no compute call is made."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith(("spmv_", "ffspmv_")) and not name.endswith("_t"):
+                names.add(name)
+    return names
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for want in ("spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
+                 "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1004_3719_gb300 as ff
+    path = ff.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_host_side_argument_errors_without_gpu():
+    # these return before any CUDA call is made
+    import paper_1004_3719_gb300 as ff
+    ff.build()
+    L = ff.lib()
+    h = ctypes.c_void_p()
+    assert L.spmv_create_hybrid(None, 1, 1, 0, None, None, None, 7, None, None) == 1
+    assert L.spmv_create_hybrid(ctypes.byref(h), -1, 1, 0, None, None, None, 7, None, None) == 1
+    assert L.spmv_apply(None, None, 1, None, 1, 1, 1, 0, None) == 1
+    assert L.spmv_block_sequence(None, None, None, 16, 10, None, None, None) == 1
+    assert L.spmv_batch_apply(-1, None, None, None, None, None) == 1
+    assert ff.status_string(6) == "device wait timed out"
+    o = ff.options_default()
+    assert o.use_pm1 == -1 and o.ell_width == -1 and o.transpose_mode == 0
+
+
+def test_options_layout_matches_header():
+    import paper_1004_3719_gb300 as ff
+    text = open(os.path.join(ROOT, "include", "ffspmv.h")).read()
+    body = text[text.index("typedef struct {"):text.index("} ffspmv_options;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:int32_t|uint32_t|int64_t)\s+([a-z_0-9]+)\s*;", body)
+    assert fields == [f for f, _ in ff.Options._fields_]

@@ -1,0 +1,160 @@
+"""GPU parity of y = alpha*A*x + beta*y and of the transpose product (Sec. 2)
+against the CPU oracle, element by element and bit-exact, for every storage
+format, several moduli, block widths and edge cases."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import rand_block, to_dev, to_host, with_modulus
+
+pytestmark = pytest.mark.gpu
+
+FORMATS = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED"]
+MODULI = [2, 3, 27, 65521, 2**31 - 1, 4294967291]
+
+
+def make(ff, A, fmt, **kw):
+    return ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, fmt), **kw)
+
+
+def check_apply(ff, M, A, nvec=1, alpha=1, beta=0, seed=0, transpose=False):
+    m = A.modulus
+    in_rows, out_rows = (A.nrows, A.ncols) if transpose else (A.ncols, A.nrows)
+    x = rand_block(seed, in_rows, nvec, m)
+    y0 = rand_block(seed + 1, out_rows, nvec, m)
+    yd = to_dev(y0)
+    if transpose:
+        M.apply_transpose(to_dev(x), yd, alpha=alpha, beta=beta)
+        want = oracle.csr_spmv_transpose(A, x, y=y0, alpha=alpha, beta=beta)
+    else:
+        M.apply(to_dev(x), yd, alpha=alpha, beta=beta)
+        want = oracle.csr_spmv(A, x, y=y0, alpha=alpha, beta=beta)
+    got = to_host(yd)
+    assert got.shape == want.shape
+    bad = np.nonzero(got != want)
+    assert bad[0].size == 0, f"{bad[0].size} mismatches, first at {bad[0][:5]}"
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("m", MODULI)
+def test_tiny_all_formats(lib, fmt, m):
+    A = gen.tiny_matrix() if m == 65521 else with_modulus(gen.tiny_matrix(), m)
+    M = make(lib, A, fmt)
+    for transpose in (False, True):
+        check_apply(lib, M, A, transpose=transpose, seed=3)
+        check_apply(lib, M, A, alpha=7 % m, beta=(m - 3) % m, transpose=transpose, seed=5)
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("nvec", [2, 3, 4, 16, 19, 32])
+def test_block_vectors(lib, fmt, nvec):
+    for m in (65521, 2**31 - 1):
+        A = with_modulus(gen.tiny_matrix(n=700, per_row=9), m, seed=nvec)
+        M = make(lib, A, fmt)
+        check_apply(lib, M, A, nvec=nvec, alpha=3, beta=2, seed=nvec)
+        check_apply(lib, M, A, nvec=nvec, transpose=True, seed=nvec + 1)
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("use_pm1", [0, 1])
+def test_powerlaw_medium(lib, fmt, use_pm1):
+    # Zipf rows (mean 16, max 3000) with a ragged tail; several tiles per bin
+    for m, pm in ((65521, 0.3), (2**31 - 1, 0.0), (3, 0.0)):
+        A = gen.powerlaw_matrix(seed=7, n=30_011, lmax=3000, m=m, pm_fraction=pm)
+        M = make(lib, A, fmt, use_pm1=use_pm1, guard_bytes=1 << 30)
+        check_apply(lib, M, A, seed=11)
+        check_apply(lib, M, A, transpose=True, alpha=5, beta=1, seed=12)
+
+
+def test_rectangular_and_empty_rows(lib):
+    A = gen.random_small(3, 517, 1283, 0.01, 65521, pm_fraction=0.4, dup=True)
+    for fmt in FORMATS:
+        M = make(lib, A, fmt)
+        check_apply(lib, M, A, seed=1)
+        check_apply(lib, M, A, transpose=True, seed=2)
+        check_apply(lib, M, A, nvec=5, alpha=9, beta=4, seed=3)
+
+
+def test_long_rows_wide_accumulator(lib):
+    # rows of (m-1) entries against x = m-1 overflow 64 bits for m ~ 2^32
+    m = 4294967291
+    lengths = np.array([0, 1, 5, 4000, 10_000, 3, 0, 77])
+    n = lengths.size
+    col = np.concatenate([np.arange(L) for L in lengths]).astype(np.int32)
+    A = gen.CSR(n, 10_000, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col,
+                np.full(lengths.sum(), m - 1, dtype=np.uint32), m)
+    for fmt in FORMATS:
+        M = make(lib, A, fmt, guard_bytes=1 << 30)
+        x = np.full(10_000, m - 1, dtype=np.uint32)
+        y = to_host(M.apply(to_dev(x)))
+        assert list(y) == [int(L) % m for L in lengths]
+        check_apply(lib, M, A, seed=4)
+        check_apply(lib, M, A, transpose=True, seed=5)
+
+
+def test_empty_matrix(lib):
+    m = 65521
+    Z = gen.CSR(6, 4, np.zeros(7, dtype=np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint32), m)
+    for fmt in FORMATS:
+        M = make(lib, Z, fmt)
+        check_apply(lib, M, Z, alpha=2, beta=3, seed=1)
+        check_apply(lib, M, Z, transpose=True, alpha=2, beta=5, seed=2)
+
+
+def test_atomic_transpose(lib):
+    A = gen.powerlaw_matrix(seed=9, n=20_000, lmax=2000, m=2**31 - 1)
+    M = lib.Matrix.from_csr(A, transpose_mode=lib.TRANSPOSE.ATOMIC)
+    for nvec in (1, 4, 17):
+        check_apply(lib, M, A, nvec=nvec, transpose=True, alpha=3, beta=7, seed=nvec)
+        check_apply(lib, M, A, nvec=nvec, transpose=True, seed=nvec + 50)
+
+
+def test_value_check_and_errors(lib):
+    import torch
+    A = gen.tiny_matrix(n=100, per_row=4)
+    M = lib.Matrix.from_csr(A, value_check=1)
+    x = np.full(100, 70000, dtype=np.uint32)            # >= m
+    with pytest.raises(lib.FFSPMVError) as e:
+        M.apply(to_dev(x))
+    assert e.value.status == 2
+    check_apply(lib, M, A, seed=3)                      # handle still usable
+    with pytest.raises(lib.FFSPMVError):
+        lib.Matrix(2, 2, [0, 1, 2], [0, 5], [1, 1], 7)  # column out of range
+    with pytest.raises(lib.FFSPMVError):
+        lib.Matrix(2, 2, [0, 1, 2], [0, 1], [1, 1], 1)  # modulus < 2
+    N = lib.Matrix.from_csr(A, transpose_mode=lib.TRANSPOSE.NONE)
+    with pytest.raises(lib.FFSPMVError) as e:
+        N.apply_transpose(to_dev(np.zeros(100, np.uint32)))
+    assert e.value.status == 5
+    y = torch.empty(100, dtype=torch.int32, device="cuda")
+    with pytest.raises(lib.FFSPMVError):
+        lib.spmv_apply(M.handle, to_dev(np.zeros(100, np.uint32)), 0, y, 1, 1)   # ldx < nvec
+
+
+def test_device_input_csr(lib):
+    import torch
+    A = gen.tiny_matrix(n=500, per_row=7)
+    M = lib.Matrix(A.nrows, A.ncols, torch.from_numpy(A.row_ptr).cuda(),
+                   torch.from_numpy(A.col).cuda(), to_dev(A.val), A.modulus)
+    check_apply(lib, M, A, seed=8)
+
+
+def test_describe_and_info(lib):
+    A = gen.powerlaw_matrix(seed=2, n=20_000, lmax=500)
+    M = make(lib, A, "HYBRID")
+    d = M.describe()
+    assert "HYBRID" in d and "ELL_R" in d
+    info = M.info()
+    assert info["nnz"] == A.nnz and info["modulus"] == A.modulus
+
+
+@pytest.mark.parametrize("m", [65521, 2**31 - 1, 3])
+def test_full_size_powerlaw(lib, m):
+    # 1M x 1M Zipf (mean 16, max 10k): the benchmark's matrix, checked whole
+    A = gen.powerlaw_matrix(seed=1002, m=m)
+    for fmt in ("HYBRID", "BINNED", "CSR"):
+        M = make(lib, A, fmt)
+        check_apply(lib, M, A, seed=21)
+        check_apply(lib, M, A, transpose=True, seed=22)
+        del M
