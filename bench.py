@@ -210,6 +210,20 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+class L2Flush:
+    """Evict L2 between timed steps: write a 256 MB buffer (twice the L2),
+    then read another one, so that the lines left in L2 are clean and no
+    write-back of the flush lands inside the next timed step."""
+
+    def __init__(self, torch):
+        self.w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.r = torch.zeros(64 << 20, dtype=torch.int32, device="cuda")
+
+    def fill_(self, v=1):
+        self.w.fill_(v)
+        self.sink = self.r.sum()
+
+
 def timed_steps(torch, fn, steps, flush, stream):
     """Sum of per-step device times (ms), L2 flushed before every step."""
     evs = []
@@ -226,6 +240,7 @@ def timed_steps(torch, fn, steps, flush, stream):
 
 
 def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
+    sp = stream.cuda_stream
     out = {}
     fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED"]
     for m in moduli:
@@ -242,7 +257,7 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
                 except ff.FFSPMVError as e:
                     row[key] = f"n/a ({e.status == 5 and 'size guard' or e})"
                     continue
-                fn = lambda: ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, stream)
+                fn = lambda: ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, sp)
                 for _ in range(3):
                     fn()
                 t = timed_steps(torch, fn, 10, flush, stream)
@@ -256,6 +271,7 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
 
 
 def extra_sequence(torch, ff, stream):
+    sp = stream.cuda_stream
     p, s = 65521, 16
     W = gen.wiedemann_matrix(seed=1003)
     n = W.nrows
@@ -266,14 +282,14 @@ def extra_sequence(torch, ff, stream):
     for mode, name in ((0, "persistent_graph"), (1, "per_launch")):
         M = ff.Matrix.from_csr(W, sequence_mode=mode, transpose_mode=ff.TRANSPOSE.NONE)
         S = torch.empty((L, s, s), dtype=torch.int32, device="cuda")
-        ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, stream)
+        ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, sp)
         torch.cuda.synchronize()
         ts = []
         for _ in range(3 if mode == 0 else 1):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, stream)
+            ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, sp)
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
@@ -285,6 +301,7 @@ def extra_sequence(torch, ff, stream):
 
 
 def extra_batch(torch, ff, stream):
+    sp = stream.cuda_stream
     probs = gen.batch_problems(seed=1004)
     mats = [ff.Matrix.from_csr(A, transpose_mode=ff.TRANSPOSE.NONE, priority_format=ff.FMT.CSR)
             for A, _ in probs]
@@ -297,11 +314,11 @@ def extra_batch(torch, ff, stream):
     work = sum(A.nnz * s for A, s in probs)
 
     def one_launch():
-        ff.spmv_batch_apply([M.handle for M in mats], xs, ys, nv, stream)
+        ff.spmv_batch_apply([M.handle for M in mats], xs, ys, nv, sp)
 
     def per_matrix():
         for M, x, y, s in zip(mats, xs, ys, nv):
-            ff.spmv_apply(M.handle, x, s, y, s, s, 1, 0, stream)
+            ff.spmv_apply(M.handle, x, s, y, s, s, 1, 0, sp)
 
     res = {"workload": f"{len(probs)} matrices, {sum(A.nnz for A, _ in probs)} nnz, "
                        f"{work} nnz*vec per pass"}
@@ -339,7 +356,7 @@ def main():
     x = torch.from_numpy(x_host.view(np.int32)).cuda()
     y = torch.empty(A.nrows, dtype=torch.int32, device="cuda")
     z = torch.empty(A.ncols, dtype=torch.int32, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
 
     def step():
         ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, sp)
@@ -414,9 +431,9 @@ def main():
     wanted = [e for e in args.extras.split(",") if e]
     del M
     torch.cuda.empty_cache()
-    for name, fn in (("formats", lambda: extra_formats(torch, ff, flush, sp)),
-                     ("sequence", lambda: extra_sequence(torch, ff, sp)),
-                     ("batch", lambda: extra_batch(torch, ff, sp))):
+    for name, fn in (("formats", lambda: extra_formats(torch, ff, flush, stream)),
+                     ("sequence", lambda: extra_sequence(torch, ff, stream)),
+                     ("batch", lambda: extra_batch(torch, ff, stream))):
         if name in wanted:
             try:
                 extra[name] = fn()

@@ -164,6 +164,10 @@ ffspmv_status spmv_destroy(ffspmv_t h);
 /* Static string naming a status code. */
 const char *ffspmv_status_string(ffspmv_status s);
 
+/* The last CUDA runtime failure seen by this host thread ("file:line: name:
+ * description"), or "" if none: the detail behind FFSPMV_ERR_CUDA. */
+const char *ffspmv_last_error(void);
+
 /* Human-readable summary of the chosen parts, bytes and bins ('\0'-terminated,
  * truncated to len). */
 ffspmv_status spmv_describe_plan(ffspmv_t h, char *buf, size_t len);

@@ -54,6 +54,8 @@ def _declare(L):
     L.ffspmv_options_default.restype = None
     L.ffspmv_status_string.argtypes = [ctypes.c_int]
     L.ffspmv_status_string.restype = ctypes.c_char_p
+    L.ffspmv_last_error.argtypes = []
+    L.ffspmv_last_error.restype = ctypes.c_char_p
     L.spmv_create_hybrid.argtypes = [ctypes.POINTER(_P), _I64, _I64, _I64, _P, _P, _P,
                                      _U32, ctypes.POINTER(Options), _P]
     L.spmv_create_hybrid.restype = ctypes.c_int
@@ -105,6 +107,8 @@ def status_string(s):
 
 def check(status, where):
     if status != 0:
+        if status == 4:
+            where = f"{where} [{lib().ffspmv_last_error().decode()}]"
         raise FFSPMVError(status, where)
 
 

@@ -74,7 +74,20 @@ ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
 
 }  // namespace
 
+namespace ff {
+static thread_local char g_last_error[320] = "";
+
+void note_cuda_error(cudaError_t e, const char *file, int line)
+{
+    const char *base = strrchr(file, '/');
+    snprintf(g_last_error, sizeof g_last_error, "%s:%d: %s: %s", base ? base + 1 : file, line,
+             cudaGetErrorName(e), cudaGetErrorString(e));
+}
+}  // namespace ff
+
 extern "C" {
+
+const char *ffspmv_last_error(void) { return ff::g_last_error; }
 
 void ffspmv_options_default(ffspmv_options *o)
 {

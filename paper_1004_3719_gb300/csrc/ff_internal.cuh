@@ -113,7 +113,8 @@ enum SegKind : int {
     SEG_CSRBLK = 1,  // one CTA per row
     SEG_ELLR = 2,    // one thread per row: DIA diagonals + ELL_R columns
     SEG_COO = 3,     // element-parallel segmented sums over sorted entries
-    SEG_EMPTY = 4    // rows with no entry: y <- beta*y
+    SEG_EMPTY = 4,   // rows with no entry: y <- beta*y
+    SEG_CSRSPLIT = 5 // long rows cut into chunks, one CTA per chunk, exact atomic sums
 };
 
 constexpr int kThreads = 256;        // threads per CTA for every plan kernel
@@ -122,6 +123,7 @@ constexpr u32 kClassShift = 30;      // +-1 class in the top two bits of col
 constexpr u32 kColMask = (1u << kClassShift) - 1u;
 constexpr u32 kPlus = 1u, kMinus = 2u;
 constexpr int kMaxSeg = 24;
+constexpr int kSplitChunk = 4096;   // entries per CTA of a split long row
 
 struct SegDesc {
     int kind;
@@ -148,6 +150,8 @@ struct SegDesc {
     const int *doff;     // DIA offsets (column - row)
     const void *dval;    // DIA values [ndiag][ld]
     long long ncols;     // columns of the matrix (DIA bounds)
+    const u32 *chunk_row;  // SEG_CSRSPLIT: local row of each chunk
+    const u32 *chunk_beg;  // SEG_CSRSPLIT: first entry of each chunk (nchunks + 1)
 };
 
 struct PlanParams {
@@ -159,10 +163,10 @@ struct PlanParams {
 
 struct Phase {
     std::vector<SegDesc> segs;
-    std::vector<u32> split_rows_host;  // COO rows shared between warp chunks
+    std::vector<u32> split_rows_host;  // rows summed through `carry` (COO, CSRSPLIT)
     const u32 *split_rows = nullptr;   // device copy
     long long nsplit = 0;
-    bool has_coo = false;
+    bool has_atomic = false;           // one vector per launch (carry holds one)
 };
 
 // One matrix plan (A or A^T).
@@ -229,8 +233,16 @@ ffspmv_status check_range(const u32 *x, long long rows, long long ld,
 
 }  // namespace ff
 
+namespace ff {
+// Records the failing CUDA call (per host thread) for ffspmv_last_error().
+void note_cuda_error(cudaError_t e, const char *file, int line);
+}
+
 #define FF_CUDA(call)                                            \
     do {                                                         \
         cudaError_t e_ = (call);                                 \
-        if (e_ != cudaSuccess) return FFSPMV_ERR_CUDA;           \
+        if (e_ != cudaSuccess) {                                 \
+            ff::note_cuda_error(e_, __FILE__, __LINE__);         \
+            return FFSPMV_ERR_CUDA;                              \
+        }                                                        \
     } while (0)

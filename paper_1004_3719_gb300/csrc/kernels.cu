@@ -22,10 +22,26 @@ Mod make_mod(u32 m, u32 alpha, u32 beta)
     return M;
 }
 
+// Matrix words are read once per product: load them without allocating in
+// L1, which is left to the gathered rows of x.
+__device__ __forceinline__ u32 ld_stream(const u32 *p)
+{
+    u32 v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ u32 ld_stream(const unsigned short *p)
+{
+    unsigned short v;
+    asm("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ u32 load_val(const void *p, long long i, int vbytes)
 {
-    if (vbytes == 2) return __ldg(reinterpret_cast<const unsigned short *>(p) + i);
-    return __ldg(reinterpret_cast<const u32 *>(p) + i);
+    if (vbytes == 2) return ld_stream(reinterpret_cast<const unsigned short *>(p) + i);
+    return ld_stream(reinterpret_cast<const u32 *>(p) + i);
 }
 
 template <int NV>
@@ -77,6 +93,56 @@ __device__ __forceinline__ void write_row(u32 *__restrict__ y, long long row,
 }
 
 // ---------------------------------------------------------------------------
+// Entries k, k + stride, ... below `end` of one CSR row, U at a time: the U
+// column words (and values) are loaded first, then the U rows of x, so that
+// U independent gathers are in flight per thread.
+#ifndef FF_UNROLL1
+#define FF_UNROLL1 2
+#endif
+#ifndef FF_MINB1
+#define FF_MINB1 8
+#endif
+
+template <int NV>
+struct Unroll {
+    static constexpr int U = NV == 1 ? FF_UNROLL1 : NV == 2 ? 4 : NV == 4 ? 2 : 1;
+};
+
+constexpr u32 kSkip = 3u;  // class of a slot past the end of the row
+
+template <class Acc, int NV>
+__device__ __forceinline__ void csr_entries(Acc (&acc)[NV], const SegDesc &S, u32 k, u32 end,
+                                            u32 stride, u32 start, u32 vbase,
+                                            const u32 *__restrict__ x, long long ldx,
+                                            bool vec4, u32 m)
+{
+    constexpr int U = Unroll<NV>::U;
+    for (; k < end; k += U * stride) {
+        u32 c[U], a[U], cls[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u32 kk = k + u * stride;
+            c[u] = 0;
+            a[u] = 0;
+            cls[u] = kSkip;
+            if (kk < end) {
+                const u32 w = ld_stream(S.col + kk);
+                cls[u] = S.pm ? (w >> kClassShift) : 0u;
+                c[u] = S.pm ? (w & kColMask) : w;
+                if (cls[u] == 0u) a[u] = load_val(S.val, (long long)vbase + (kk - start), S.vbytes);
+            }
+        }
+        u32 xv[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (cls[u] != kSkip) load_x<NV>(x, c[u], ldx, xv[u], vec4);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (cls[u] != kSkip) apply_entry<NV>(acc, cls[u], a[u], xv[u], m);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CSR, `group` lanes per row (a power of two up to 32).
 template <class Acc, int NV>
 __device__ void seg_csr(const SegDesc &S, long long lb, const u32 *__restrict__ x,
@@ -94,18 +160,7 @@ __device__ void seg_csr(const SegDesc &S, long long lb, const u32 *__restrict__ 
     if (active) {
         const u32 start = __ldg(S.ptr + r), end = __ldg(S.ptr + r + 1);
         const u32 vbase = S.vptr ? __ldg(S.vptr + r) : start;
-        for (u32 k = start + lane; k < end; k += G) {
-            u32 c = __ldg(S.col + k);
-            u32 cls = 0;
-            if (S.pm) {
-                cls = c >> kClassShift;
-                c &= kColMask;
-            }
-            u32 a = (cls == 0u) ? load_val(S.val, (long long)vbase + (k - start), S.vbytes) : 0u;
-            u32 xv[NV];
-            load_x<NV>(x, c, ldx, xv, vec4);
-            apply_entry<NV>(acc, cls, a, xv, M.m);
-        }
+        csr_entries<Acc, NV>(acc, S, start + lane, end, (u32)G, start, vbase, x, ldx, vec4, M.m);
     }
     u64 part[NV];
 #pragma unroll
@@ -120,35 +175,11 @@ __device__ void seg_csr(const SegDesc &S, long long lb, const u32 *__restrict__ 
     }
 }
 
-// ---------------------------------------------------------------------------
-// CSR, one CTA per row (long rows).
-template <class Acc, int NV>
-__device__ void seg_csrblk(const SegDesc &S, long long lb, const u32 *__restrict__ x,
-                           long long ldx, u32 *__restrict__ y, long long ldy,
-                           const Mod &M, bool vec4)
+// Sum of `part` over the CTA, valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(u64 (&part)[NV])
 {
     __shared__ u64 red[kThreads / 32][NV];
-    const long long r = lb;
-    const u32 start = __ldg(S.ptr + r), end = __ldg(S.ptr + r + 1);
-    const u32 vbase = S.vptr ? __ldg(S.vptr + r) : start;
-    Acc acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v].zero();
-    for (u32 k = start + threadIdx.x; k < end; k += kThreads) {
-        u32 c = __ldg(S.col + k);
-        u32 cls = 0;
-        if (S.pm) {
-            cls = c >> kClassShift;
-            c &= kColMask;
-        }
-        u32 a = (cls == 0u) ? load_val(S.val, (long long)vbase + (k - start), S.vbytes) : 0u;
-        u32 xv[NV];
-        load_x<NV>(x, c, ldx, xv, vec4);
-        apply_entry<NV>(acc, cls, a, xv, M.m);
-    }
-    u64 part[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) part[v] = acc[v].partial(M);
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) part[v] += __shfl_xor_sync(0xffffffffu, part[v], off);
@@ -162,12 +193,59 @@ __device__ void seg_csrblk(const SegDesc &S, long long lb, const u32 *__restrict
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            u64 s = 0;
-            for (int i = 0; i < kThreads / 32; ++i) s += red[i][v];
-            part[v] = s;
+            u64 t = 0;
+            for (int i = 0; i < kThreads / 32; ++i) t += red[i][v];
+            part[v] = t;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CSR, one CTA per row.
+template <class Acc, int NV>
+__device__ void seg_csrblk(const SegDesc &S, long long lb, const u32 *__restrict__ x,
+                           long long ldx, u32 *__restrict__ y, long long ldy,
+                           const Mod &M, bool vec4)
+{
+    const long long r = lb;
+    const u32 start = __ldg(S.ptr + r), end = __ldg(S.ptr + r + 1);
+    const u32 vbase = S.vptr ? __ldg(S.vptr + r) : start;
+    Acc acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v].zero();
+    csr_entries<Acc, NV>(acc, S, start + threadIdx.x, end, (u32)kThreads, start, vbase, x, ldx,
+                         vec4, M.m);
+    u64 part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v] = acc[v].partial(M);
+    block_sum<NV>(part);
+    if (threadIdx.x == 0) {
         const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
         write_row<NV>(y, row, ldy, part, S.accum, M);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Long rows cut into chunks of at most kSplitChunk entries, one CTA per
+// chunk; each CTA adds its reduced partial sum into carry[row] with an exact
+// 64-bit atomic and a second launch finishes the rows.  One vector per launch.
+template <class Acc>
+__device__ void seg_csrsplit(const SegDesc &S, long long lb, const u32 *__restrict__ x,
+                             long long ldx, const Mod &M, u64 *__restrict__ carry)
+{
+    const u32 r = __ldg(S.chunk_row + lb);
+    const u32 b = __ldg(S.chunk_beg + lb), e = __ldg(S.chunk_beg + lb + 1);
+    const u32 start = __ldg(S.ptr + r);
+    const u32 vbase = S.vptr ? __ldg(S.vptr + r) : start;
+    Acc acc[1];
+    acc[0].zero();
+    csr_entries<Acc, 1>(acc, S, b + threadIdx.x, e, (u32)kThreads, start, vbase, x, ldx, false,
+                        M.m);
+    u64 part[1] = {acc[0].partial(M)};
+    block_sum<1>(part);
+    if (threadIdx.x == 0) {
+        const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
+        atomicAdd(carry + row, (u64)red64(part[0], M));
     }
 }
 
@@ -179,6 +257,7 @@ __device__ void seg_ellr(const SegDesc &S, long long lb, const u32 *__restrict__
                          long long ldx, u32 *__restrict__ y, long long ldy,
                          const Mod &M, bool vec4)
 {
+    constexpr int U = Unroll<NV>::U;
     const long long r = lb * kThreads + threadIdx.x;
     if (r >= S.nrows) return;
     const long long row = S.rows ? (long long)__ldg(S.rows + r) : S.row0 + r;
@@ -195,18 +274,28 @@ __device__ void seg_ellr(const SegDesc &S, long long lb, const u32 *__restrict__
         }
     }
     const int n = S.rownb ? (int)__ldg(S.rownb + r) : S.width;
-    for (int j = 0; j < n; ++j) {
-        const long long idx = (long long)j * S.ld + r;
-        u32 c = __ldg(S.col + idx);
-        u32 cls = 0;
-        if (S.pm) {
-            cls = c >> kClassShift;
-            c &= kColMask;
+    for (int j = 0; j < n; j += U) {
+        u32 c[U], a[U], cls[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = 0;
+            a[u] = 0;
+            cls[u] = kSkip;
+            if (j + u < n) {
+                const long long idx = (long long)(j + u) * S.ld + r;
+                const u32 w = ld_stream(S.col + idx);
+                cls[u] = S.pm ? (w >> kClassShift) : 0u;
+                c[u] = S.pm ? (w & kColMask) : w;
+                if (cls[u] == 0u) a[u] = load_val(S.val, idx, S.vbytes);
+            }
         }
-        u32 a = (cls == 0u) ? load_val(S.val, idx, S.vbytes) : 0u;
-        u32 xv[NV];
-        load_x<NV>(x, c, ldx, xv, vec4);
-        apply_entry<NV>(acc, cls, a, xv, M.m);
+        u32 xv[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (cls[u] != kSkip) load_x<NV>(x, c[u], ldx, xv[u], vec4);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (cls[u] != kSkip) apply_entry<NV>(acc, cls[u], a[u], xv[u], M.m);
     }
     u64 part[NV];
 #pragma unroll
@@ -325,22 +414,44 @@ __device__ void seg_empty(const SegDesc &S, long long lb, u32 *__restrict__ y,
 }
 
 template <class Acc, int NV>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, NV == 1 ? FF_MINB1 : 2)
 k_plan(const __grid_constant__ PlanParams P, const u32 *__restrict__ x,
        long long ldx, u32 *__restrict__ y, long long ldy, const Mod M,
        u64 *__restrict__ carry, int vec4)
 {
-    const long long b = blockIdx.x;
-    int s = 0;
-    while (s + 1 < P.nseg && b >= P.seg[s + 1].block0) ++s;
-    const SegDesc &S = P.seg[s];
-    const long long lb = b - S.block0;
+    // The descriptor of this CTA's segment is copied once into shared memory
+    // and from there into registers: indexing the parameter table with a
+    // run-time segment number inside the loops would turn every field access
+    // into a constant-bank load.
+    __shared__ SegDesc sdesc;
+    __shared__ int sidx;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = P.nseg - 1;
+        const long long b = blockIdx.x;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.seg[mid].block0 <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        sidx = lo;
+    }
+    __syncthreads();
+    constexpr int W = (int)(sizeof(SegDesc) / sizeof(u32));
+    if (threadIdx.x < W)
+        reinterpret_cast<u32 *>(&sdesc)[threadIdx.x] =
+            reinterpret_cast<const u32 *>(&P.seg[sidx])[threadIdx.x];
+    __syncthreads();
+    const SegDesc &S = sdesc;
+    const long long lb = (long long)blockIdx.x - S.block0;
     switch (S.kind) {
     case SEG_CSR: seg_csr<Acc, NV>(S, lb, x, ldx, y, ldy, M, vec4 != 0); break;
     case SEG_CSRBLK: seg_csrblk<Acc, NV>(S, lb, x, ldx, y, ldy, M, vec4 != 0); break;
     case SEG_ELLR: seg_ellr<Acc, NV>(S, lb, x, ldx, y, ldy, M, vec4 != 0); break;
     case SEG_COO:
         if constexpr (NV == 1) seg_coo(S, lb, x, ldx, y, ldy, M, carry);
+        break;
+    case SEG_CSRSPLIT:
+        if constexpr (NV == 1) seg_csrsplit<Acc>(S, lb, x, ldx, M, carry);
         break;
     case SEG_EMPTY: seg_empty<NV>(S, lb, y, ldy, M); break;
     default: break;
@@ -399,9 +510,9 @@ static PlanParams params_of(const Phase &ph, int acc_wide)
     return pp;
 }
 
-static int next_chunk(int left, bool has_coo)
+static int next_chunk(int left, bool has_atomic)
 {
-    if (has_coo) return 1;
+    if (has_atomic) return 1;
     return left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
 }
 
@@ -411,7 +522,7 @@ long long count_plan_launches(const Plan &P, int nvec)
     long long n = 0;
     for (const Phase &ph : P.phases) {
         if (ph.segs.empty()) continue;
-        for (int c0 = 0; c0 < nvec; c0 += next_chunk(nvec - c0, ph.has_coo))
+        for (int c0 = 0; c0 < nvec; c0 += next_chunk(nvec - c0, ph.has_atomic))
             n += 1 + (ph.nsplit > 0 ? 1 : 0);
     }
     return n;
@@ -429,7 +540,7 @@ ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
         if (pp.total_blocks <= 0) continue;
         int c0 = 0;
         while (c0 < nvec) {
-            int nv = next_chunk(nvec - c0, ph.has_coo);
+            int nv = next_chunk(nvec - c0, ph.has_atomic);
             const u32 *xc = x + c0;
             u32 *yc = y + c0;
             bool vec4 = nv >= 4 && (ldx % 4 == 0) && ((uintptr_t)xc % 16 == 0);

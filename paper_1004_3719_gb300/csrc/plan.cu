@@ -52,6 +52,7 @@ struct SegBuild {
     SegDesc d;
     size_t o_rows = kNo, o_ptr = kNo, o_vptr = kNo, o_col = kNo, o_val = kNo;
     size_t o_rowid = kNo, o_rownb = kNo, o_doff = kNo, o_dval = kNo;
+    size_t o_crow = kNo, o_cbeg = kNo;
     std::vector<u32> split;
     SegBuild() { memset(&d, 0, sizeof(d)); }
 };
@@ -104,7 +105,7 @@ bool want_pm(int use_pm1, long long npm, long long total, long long ncols)
 // ---------------------------------------------------------------------------
 // CSR-like segment (SEG_CSR / SEG_CSRBLK) over rows `R` of matrix `A`.
 bool make_csr(Blob &B, const Mat &A, const Rows &R, int kind, int group,
-              int use_pm1, int accum, u32 m, SegBuild &S)
+              int use_pm1, int accum, u32 m, SegBuild &S, std::vector<u32> *ptr_out = nullptr)
 {
     long long total = 0, npm = 0;
     for (long long r = 0; r < R.n; ++r) {
@@ -161,9 +162,60 @@ bool make_csr(Blob &B, const Mat &A, const Rows &R, int kind, int group,
     d.nblocks = kind == SEG_CSRBLK ? R.n : (R.n + (kThreads / group) - 1) / (kThreads / group);
     if (!R.ids.empty()) S.o_rows = B.putv(R.ids);
     S.o_ptr = B.putv(ptr);
+    if (ptr_out) *ptr_out = ptr;
     if (!vptr.empty()) S.o_vptr = B.putv(vptr);
     S.o_col = B.putv(col);
     if (vb) S.o_val = B.putv(val);
+    return true;
+}
+
+// Long rows `R` cut into chunks of kSplitChunk entries (SEG_CSRSPLIT).
+bool make_csrsplit(Blob &B, const Mat &A, const Rows &R, int use_pm1, int accum, u32 m,
+                   SegBuild &S)
+{
+    std::vector<u32> ptr;
+    if (!make_csr(B, A, R, SEG_CSRSPLIT, 1, use_pm1, accum, m, S, &ptr)) return false;
+    std::vector<u32> crow, cbeg;
+    for (long long r = 0; r < R.n; ++r)
+        for (u32 k = ptr[r]; k < ptr[r + 1]; k += kSplitChunk) {
+            crow.push_back((u32)r);
+            cbeg.push_back(k);
+        }
+    cbeg.push_back(ptr[R.n]);
+    S.d.kind = SEG_CSRSPLIT;
+    S.d.nblocks = (long long)crow.size();
+    S.o_crow = B.putv(crow);
+    S.o_cbeg = B.putv(cbeg);
+    for (long long r = 0; r < R.n; ++r) S.split.push_back((u32)R.at(r));
+    return true;
+}
+
+// CSR over rows `R`, with the rows longer than `split_at` entries moved to a
+// SEG_CSRSPLIT segment.  Appends one or two segments to `out`.
+bool make_csr_with_split(Blob &B, const Mat &A, const Rows &R, int group, int use_pm1,
+                         int accum, u32 m, long long split_at, std::vector<SegBuild> &out)
+{
+    Rows shortr, longr;
+    for (long long r = 0; r < R.n; ++r) {
+        long long i = R.at(r);
+        (A.ptr[i + 1] - A.ptr[i] > split_at ? longr : shortr).ids.push_back((u32)i);
+    }
+    shortr.n = (long long)shortr.ids.size();
+    longr.n = (long long)longr.ids.size();
+    if (longr.n == 0) {
+        SegBuild s;
+        if (!make_csr(B, A, R, SEG_CSR, group, use_pm1, accum, m, s)) return false;
+        out.push_back(s);
+        return true;
+    }
+    if (shortr.n) {
+        SegBuild s;
+        if (!make_csr(B, A, shortr, SEG_CSR, group, use_pm1, accum, m, s)) return false;
+        out.push_back(s);
+    }
+    SegBuild s;
+    if (!make_csrsplit(B, A, longr, use_pm1, accum, m, s)) return false;
+    out.push_back(s);
     return true;
 }
 
@@ -445,7 +497,7 @@ ffspmv_status finish(Plan &P, Blob &B, std::vector<std::vector<SegBuild>> &phase
         std::vector<u32> all;
         for (auto &s : phases[p]) {
             all.insert(all.end(), s.split.begin(), s.split.end());
-            if (s.d.kind == SEG_COO) any_coo = true;
+            if (s.d.kind == SEG_COO || s.d.kind == SEG_CSRSPLIT) any_coo = true;
         }
         if (!all.empty()) o_split[p] = B.putv(all);
         Phase ph;
@@ -480,9 +532,11 @@ ffspmv_status finish(Plan &P, Blob &B, std::vector<std::vector<SegBuild>> &phase
             d.rownb = (const u32 *)at(s.o_rownb);
             d.doff = (const int *)at(s.o_doff);
             d.dval = at(s.o_dval);
+            d.chunk_row = (const u32 *)at(s.o_crow);
+            d.chunk_beg = (const u32 *)at(s.o_cbeg);
             d.block0 = block;
             block += d.nblocks;
-            if (d.kind == SEG_COO) ph.has_coo = true;
+            if (d.kind == SEG_COO || d.kind == SEG_CSRSPLIT) ph.has_atomic = true;
             ph.segs.push_back(d);
         }
     }
@@ -503,6 +557,7 @@ const char *kind_name(const SegDesc &d)
     case SEG_CSRBLK: return "CSR-CTA";
     case SEG_ELLR: return d.width ? (d.ndiag ? "DIA+ELL_R" : "ELL_R") : "DIA";
     case SEG_COO: return "COO";
+    case SEG_CSRSPLIT: return "CSR-split";
     default: return "EMPTY";
     }
 }
@@ -554,11 +609,14 @@ BinChoice heuristic_bin_choice(int b, double pm_fraction, int use_pm1)
     if (U <= 8) {
         c.kind = SEG_ELLR;
         c.group = 1;
-    } else if (U <= 1024) {
+    } else if (U <= 256) {
         c.kind = SEG_CSR;
         c.group = (int)std::min<long long>(32, U / 2);
-    } else {
+    } else if (U <= 2048) {
         c.kind = SEG_CSRBLK;
+        c.group = 32;
+    } else {
+        c.kind = SEG_CSRSPLIT;
         c.group = 32;
     }
     c.pm = use_pm1 == 1 ? 1 : use_pm1 == 0 ? 0 : (pm_fraction >= 0.1 ? 1 : 0);
@@ -697,15 +755,17 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
             const long long tnnz = (long long)T.col.size();
             SegBuild s;
             bool ok;
-            if (tf.n * 2 < nrows) {
-                ok = make_csr(B, T, tf, SEG_CSR, default_group(T, tf.n), upm, acc, m, s);  // COO_S
+            if (tf.n * 2 < nrows) {  // COO_S: CSR over the non-empty residue rows
+                ok = make_csr_with_split(B, T, tf, default_group(T, tf.n), upm, acc, m,
+                                         kSplitChunk / 2, ph);
             } else if (tnnz < 2 * tf.n) {
                 ok = make_coo(B, T, tf, upm, acc, m, s);
+                if (ok) ph.push_back(s);
             } else {
-                ok = make_csr(B, T, all_rows(nrows), SEG_CSR, default_group(T, tf.n), upm, acc, m, s);
+                ok = make_csr_with_split(B, T, all_rows(nrows), default_group(T, tf.n), upm, acc,
+                                         m, kSplitChunk / 2, ph);
             }
             if (!ok) return FFSPMV_ERR_UNSUPPORTED;
-            ph.push_back(s);
             if (!has_first && !(tf.n * 2 >= nrows && tnnz >= 2 * tf.n)) {
                 Rows e2;
                 for (long long i = 0; i < nrows; ++i)
@@ -752,6 +812,8 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                 ok = make_ellr(B, A, R, {}, nullptr, pmode, 0, m, guard, s);
             else if (c.kind == SEG_COO)
                 ok = make_coo(B, A, R, pmode, 0, m, s);
+            else if (c.kind == SEG_CSRSPLIT)
+                ok = make_csrsplit(B, A, R, pmode, 0, m, s);
             else
                 ok = make_csr(B, A, R, c.kind == SEG_CSRBLK ? SEG_CSRBLK : SEG_CSR,
                               std::max(1, std::min(32, c.group)), pmode, 0, m, s);

@@ -29,12 +29,14 @@ namespace ff {
 namespace {
 
 constexpr int kSeqThreads = 512;
-constexpr int kS = 16;                          // block width of the persistent kernel
-constexpr int kCPT = 4;                         // components per thread
-constexpr int kTPR = kS / kCPT;                 // threads per row
-constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 128
-constexpr int kKSteps = kRowsPerPass / 16;        // 8 k-steps of 16 rows
-constexpr unsigned kDefaultSpins = 1u << 22;      // x ~256 ns sleeps: about a second
+constexpr int kS = 16;                            // block width of the persistent kernel
+constexpr int kCPT = 8;                           // components per thread
+constexpr int kTPR = kS / kCPT;                   // threads per row
+constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 256
+constexpr int kKSteps = kRowsPerPass / 16;        // 16 k-steps of 16 rows
+constexpr int kMaxEnt = 16;                       // DIA + ELL_R entries per row
+constexpr int kVsStride = 20;                     // halves per staged row (no bank conflicts)
+constexpr unsigned kDefaultSpins = 1u << 22;      // x <= 64 ns sleeps: well under a second
 
 struct SeqArgs {
     long long n;
@@ -46,7 +48,7 @@ struct SeqArgs {
     const u32 *col;
     const unsigned short *val;
     const u32 *rownb;
-    const unsigned short *Xh;  // n x 16
+    const uint4 *XF;           // X limbs in MMA A-fragment order: [n/16][limb][lane]
     unsigned short *V0, *V1;   // n x 16
     u32 *partial;              // [2][nblocks][256]
     u32 *S;
@@ -91,18 +93,18 @@ __device__ bool grid_barrier(const SeqArgs &a, bool skip)
             } else {
                 unsigned it = 0;
                 while (ld_acquire(a.bar + 1) == gen) {
-                    if (ld_volatile_int(a.status) != 0 || ++it > a.spin_limit) {
+                    if (++it > a.spin_limit || ((it & 255u) == 0 && ld_volatile_int(a.status) != 0)) {
                         atomicExch(a.status, 1);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(256);
+                    if (it > 64) __nanosleep(64);
                 }
             }
         } else {
             // test hook: never arrive; wait (bounded) for the others to give up
             unsigned it = 0;
-            while (ld_volatile_int(a.status) == 0 && ++it <= a.spin_limit) __nanosleep(256);
+            while (ld_volatile_int(a.status) == 0 && ++it <= a.spin_limit) __nanosleep(64);
             atomicExch(a.status, 1);
             ok = 0;
         }
@@ -113,190 +115,207 @@ __device__ bool grid_barrier(const SeqArgs &a, bool skip)
     return s_ok != 0;
 }
 
-__device__ __forceinline__ unsigned pack_half2(unsigned lo_elem, unsigned hi_elem)
+// Two 8-bit integers (bits 0-7 and 16-23 of p) as an exact f16x2 pair:
+// 0x6400 | b is the half 1024 + b, and subtracting 1024 is exact.
+__device__ __forceinline__ u32 bytes_to_half2(u32 p)
 {
-    __half2 h = __halves2half2(__uint2half_rn(lo_elem), __uint2half_rn(hi_elem));
-    return *reinterpret_cast<unsigned *>(&h);
+    u32 r;
+    asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(p | 0x64006400u), "r"(0x64006400u));
+    return r;
 }
 
-__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&A)[4],
-                                         const unsigned (&B)[2])
+// An exact non-negative integer below 2^23 held in an fp32, as u32.
+__device__ __forceinline__ u32 f32_to_u32(float f)
+{
+    return __float_as_uint(f + 8388608.0f) - 0x4B000000u;
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint4 &A, u32 b0, u32 b1)
 {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
         "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};"
         : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-        : "r"(A[0]), "r"(A[1]), "r"(A[2]), "r"(A[3]), "r"(B[0]), "r"(B[1]),
+        : "r"(A.x), "r"(A.y), "r"(A.z), "r"(A.w), "r"(b0), "r"(b1),
           "f"(0.f), "f"(0.f), "f"(0.f), "f"(0.f));
 }
 
-struct SeqSmem {
-    // limbs of one pass: [limb][row][component], component padded to 18 halves
-    unsigned short xs[2][kRowsPerPass][kS + 2];
-    unsigned short vs[2][kRowsPerPass][kS + 2];
-    unsigned long long acc[kS * kS];
-    unsigned long long red[kSeqThreads / 32];
+struct __align__(16) SeqSmem {
+    union {
+        unsigned short vs[2][kRowsPerPass][kVsStride];  // staged V rows, double buffered
+        u32 red[kSeqThreads / 32][kS * kS];             // per-warp partial projections
+    };
+    int doff[kMaxEnt];
 };
 
-// Project the pass tile held in shared memory: warp w takes k-step (w & 7)
-// and limb pairs 2*(w>>3), 2*(w>>3)+1 (pair index = 2*x_limb + v_limb).
-__device__ __forceinline__ void project_tile(SeqSmem &sm, unsigned long long (&pacc)[2][4])
+// V_out rows [r0, r1) = A * V_in (when `compute`), and, when `project`, the
+// partial X^T V_out over those rows accumulated in pacc.  Two threads share a
+// row (8 components each); warp w then runs k-step w of every 256-row pass
+// with both X limbs against both V limbs (8 MMAs).  Indices are 32-bit: the
+// layout guarantees 16 n < 2^31.
+__device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned short *Vin,
+                                 unsigned short *Vout, int r0, int r1, bool compute,
+                                 bool project, u64 (&pacc)[2][2][4])
 {
+    const int rip = threadIdx.x / kTPR;
+    const int c0 = (threadIdx.x % kTPR) * kCPT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int ks = w & (kKSteps - 1);
-    const int k0 = ks * 16;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int lp = 2 * (w >> 3) + q;
-        const int xl = lp >> 1, vl = lp & 1;
-        const unsigned long long wgt = (xl ? 256ull : 1ull) * (vl ? 256ull : 1ull);
-        unsigned A[4];
-        A[0] = pack_half2(sm.xs[xl][k0 + 2 * t][g], sm.xs[xl][k0 + 2 * t + 1][g]);
-        A[1] = pack_half2(sm.xs[xl][k0 + 2 * t][g + 8], sm.xs[xl][k0 + 2 * t + 1][g + 8]);
-        A[2] = pack_half2(sm.xs[xl][k0 + 2 * t + 8][g], sm.xs[xl][k0 + 2 * t + 9][g]);
-        A[3] = pack_half2(sm.xs[xl][k0 + 2 * t + 8][g + 8], sm.xs[xl][k0 + 2 * t + 9][g + 8]);
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int n = nt * 8 + g;
-            unsigned B[2];
-            B[0] = pack_half2(sm.vs[vl][k0 + 2 * t][n], sm.vs[vl][k0 + 2 * t + 1][n]);
-            B[1] = pack_half2(sm.vs[vl][k0 + 2 * t + 8][n], sm.vs[vl][k0 + 2 * t + 9][n]);
-            float d[4];
-            mma16816(d, A, B);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) pacc[nt][e] += wgt * (unsigned long long)__float2uint_rn(d[e]);
-        }
-    }
-}
-
-// V_out rows [r0, r1) = A * V_in, and (if `project`) the partial X^T V_out
-// over those rows into sm.acc.
-__device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned short *Vin,
-                                 unsigned short *Vout, long long r0, long long r1,
-                                 bool compute, bool project)
-{
-    const int rip = threadIdx.x / kTPR;     // row in pass
-    const int c0 = (threadIdx.x % kTPR) * kCPT;
-    unsigned long long pacc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    for (long long base = r0; base < r1; base += kRowsPerPass) {
-        const long long row = base + rip;
-        u32 out[kCPT] = {0, 0, 0, 0};
+    const int nd = a.ndiag, n = (int)a.n, ld = (int)a.ld;
+    int pass = 0;
+    for (int base = r0; base < r1; base += kRowsPerPass, ++pass) {
+        const int row = base + rip;
+        uint4 outq = make_uint4(0u, 0u, 0u, 0u);
         if (row < r1) {
             if (compute) {
-                unsigned long long acc[kCPT] = {0, 0, 0, 0};
-                for (int d = 0; d < a.ndiag; ++d) {
-                    const long long j = row + __ldg(a.doff + d);
-                    if (j >= 0 && j < a.n) {
-                        const u32 v = __ldg(a.dval + (long long)d * a.ld + row);
-                        const uint2 q = __ldcg(reinterpret_cast<const uint2 *>(Vin + j * kS + c0));
-                        acc[0] += (unsigned long long)v * (q.x & 0xffffu);
-                        acc[1] += (unsigned long long)v * (q.x >> 16);
-                        acc[2] += (unsigned long long)v * (q.y & 0xffffu);
-                        acc[3] += (unsigned long long)v * (q.y >> 16);
+                const int ntot = nd + (a.rownb ? (int)__ldg(a.rownb + row) : a.width);
+                u64 acc[kCPT];
+#pragma unroll
+                for (int k = 0; k < kCPT; ++k) acc[k] = 0;
+#pragma unroll
+                for (int e0 = 0; e0 < kMaxEnt; e0 += 4) {
+                    if (e0 >= ntot) break;
+                    uint4 q[4];
+                    u32 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u;
+                        q[u] = make_uint4(0u, 0u, 0u, 0u);
+                        v[u] = 0;
+                        if (e < nd) {
+                            const int j = row + sm.doff[e];
+                            if ((unsigned)j < (unsigned)n) {
+                                v[u] = __ldg(a.dval + e * ld + row);
+                                q[u] = __ldcg(reinterpret_cast<const uint4 *>(Vin + j * kS + c0));
+                            }
+                        } else if (e < ntot) {
+                            const int idx = (e - nd) * ld + row;
+                            const int j = (int)__ldg(a.col + idx);
+                            v[u] = __ldg(a.val + idx);
+                            q[u] = __ldcg(reinterpret_cast<const uint4 *>(Vin + j * kS + c0));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const u32 qq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            acc[2 * k] += (u64)v[u] * (qq[k] & 0xffffu);
+                            acc[2 * k + 1] += (u64)v[u] * (qq[k] >> 16);
+                        }
                     }
                 }
-                const int nb = a.rownb ? (int)__ldg(a.rownb + row) : a.width;
-                for (int e = 0; e < nb; ++e) {
-                    const long long idx = (long long)e * a.ld + row;
-                    const long long j = __ldg(a.col + idx);
-                    const u32 v = __ldg(a.val + idx);
-                    const uint2 q = __ldcg(reinterpret_cast<const uint2 *>(Vin + j * kS + c0));
-                    acc[0] += (unsigned long long)v * (q.x & 0xffffu);
-                    acc[1] += (unsigned long long)v * (q.x >> 16);
-                    acc[2] += (unsigned long long)v * (q.y & 0xffffu);
-                    acc[3] += (unsigned long long)v * (q.y >> 16);
-                }
-#pragma unroll
-                for (int v = 0; v < kCPT; ++v) out[v] = red64(acc[v], a.M);
-                uint2 st;
-                st.x = out[0] | (out[1] << 16);
-                st.y = out[2] | (out[3] << 16);
-                *reinterpret_cast<uint2 *>(Vout + row * kS + c0) = st;
+                outq.x = red64(acc[0], a.M) | (red64(acc[1], a.M) << 16);
+                outq.y = red64(acc[2], a.M) | (red64(acc[3], a.M) << 16);
+                outq.z = red64(acc[4], a.M) | (red64(acc[5], a.M) << 16);
+                outq.w = red64(acc[6], a.M) | (red64(acc[7], a.M) << 16);
+                *reinterpret_cast<uint4 *>(Vout + row * kS + c0) = outq;
             } else {
-                const uint2 q = __ldcg(reinterpret_cast<const uint2 *>(Vin + row * kS + c0));
-                out[0] = q.x & 0xffffu;
-                out[1] = q.x >> 16;
-                out[2] = q.y & 0xffffu;
-                out[3] = q.y >> 16;
+                outq = __ldcg(reinterpret_cast<const uint4 *>(Vin + row * kS + c0));
             }
         }
         if (!project) continue;
-        // stage this pass's limbs
-        uint2 xq = make_uint2(0u, 0u);
-        if (row < r1) xq = __ldg(reinterpret_cast<const uint2 *>(a.Xh + row * kS + c0));
-        const u32 xv[kCPT] = {xq.x & 0xffffu, xq.x >> 16, xq.y & 0xffffu, xq.y >> 16};
+        unsigned short(*vs)[kVsStride] = sm.vs[pass & 1];
+        *reinterpret_cast<uint2 *>(&vs[rip][c0]) = make_uint2(outq.x, outq.y);
+        *reinterpret_cast<uint2 *>(&vs[rip][c0 + 4]) = make_uint2(outq.z, outq.w);
+        __syncthreads();
+        const int q16 = (base >> 4) + w;
+        if (q16 * 16 < r1) {
+            const uint4 A0 = __ldg(a.XF + ((size_t)q16 * 2 + 0) * 32 + lane);
+            const uint4 A1 = __ldg(a.XF + ((size_t)q16 * 2 + 1) * 32 + lane);
+            const int k0 = w * 16;
 #pragma unroll
-        for (int v = 0; v < kCPT; ++v) {
-            sm.xs[0][rip][c0 + v] = (unsigned short)(xv[v] & 255u);
-            sm.xs[1][rip][c0 + v] = (unsigned short)(xv[v] >> 8);
-            sm.vs[0][rip][c0 + v] = (unsigned short)(out[v] & 255u);
-            sm.vs[1][rip][c0 + v] = (unsigned short)(out[v] >> 8);
+            for (int nt = 0; nt < 2; ++nt) {
+                const int nn = nt * 8 + g;
+                const u32 p0 = vs[k0 + 2 * t][nn] | ((u32)vs[k0 + 2 * t + 1][nn] << 16);
+                const u32 p1 = vs[k0 + 2 * t + 8][nn] | ((u32)vs[k0 + 2 * t + 9][nn] << 16);
+#pragma unroll
+                for (int vl = 0; vl < 2; ++vl) {
+                    const u32 b0 = bytes_to_half2(vl ? (p0 >> 8) & 0x00ff00ffu : p0 & 0x00ff00ffu);
+                    const u32 b1 = bytes_to_half2(vl ? (p1 >> 8) & 0x00ff00ffu : p1 & 0x00ff00ffu);
+                    float d0[4], d1[4];
+                    mma16816(d0, A0, b0, b1);
+                    mma16816(d1, A1, b0, b1);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        pacc[vl][nt][e] += (u64)f32_to_u32(d0[e]);
+                        pacc[vl][nt][e] += (u64)f32_to_u32(d1[e]) << 8;
+                    }
+                }
+            }
         }
-        __syncthreads();
-        project_tile(sm, pacc);
-        __syncthreads();
     }
-    if (!project) return;
-    const int lane = threadIdx.x & 31;
+}
+
+// Add the warps' fragments into sm.acc, then write this CTA's partial
+// projection (reduced) and clear the accumulators.
+__device__ void publish_partial(const SeqArgs &a, SeqSmem &sm, int buf, u64 (&pacc)[2][2][4])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
+    __syncthreads();  // the last pass's MMAs have read the staged rows
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
         const int b = nt * 8 + 2 * t;
-        atomicAdd(&sm.acc[g * kS + b], pacc[nt][0]);
-        atomicAdd(&sm.acc[g * kS + b + 1], pacc[nt][1]);
-        atomicAdd(&sm.acc[(g + 8) * kS + b], pacc[nt][2]);
-        atomicAdd(&sm.acc[(g + 8) * kS + b + 1], pacc[nt][3]);
+        u32 c[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            c[e] = red64(pacc[0][nt][e] + (pacc[1][nt][e] << 8), a.M);  // V limb weights 1, 256
+            pacc[0][nt][e] = pacc[1][nt][e] = 0;
+        }
+        sm.red[w][g * kS + b] = c[0];
+        sm.red[w][g * kS + b + 1] = c[1];
+        sm.red[w][(g + 8) * kS + b] = c[2];
+        sm.red[w][(g + 8) * kS + b + 1] = c[3];
     }
-}
-
-// Write this CTA's partial projection (reduced) and clear the accumulator.
-__device__ void publish_partial(const SeqArgs &a, SeqSmem &sm, int buf)
-{
     __syncthreads();
     u32 *dst = a.partial + ((size_t)buf * gridDim.x + blockIdx.x) * (kS * kS);
-    for (int t = threadIdx.x; t < kS * kS; t += blockDim.x) {
-        dst[t] = red64(sm.acc[t], a.M);
-        sm.acc[t] = 0;
+    for (int o = threadIdx.x; o < kS * kS; o += blockDim.x) {
+        u64 tot = 0;
+#pragma unroll
+        for (int i = 0; i < kSeqThreads / 32; ++i) tot += sm.red[i][o];
+        dst[o] = red64(tot, a.M);
     }
-    __syncthreads();
+    __syncthreads();  // sm.red aliases the staging rows of the next step
 }
 
-// S_step[o] = sum over CTAs of their partials (mod p), outputs split over CTAs.
-__device__ void reduce_step(const SeqArgs &a, SeqSmem &sm, int buf, long long step)
+// S_step[o] = sum over CTAs of their partials (mod p); one warp per output.
+__device__ void reduce_step(const SeqArgs &a, int buf, long long step)
 {
     const int nb = gridDim.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
     const u32 *src = a.partial + (size_t)buf * nb * (kS * kS);
-    for (int o = blockIdx.x; o < kS * kS; o += nb) {
-        unsigned long long s = 0;
-        for (int c = threadIdx.x; c < nb; c += blockDim.x) s += __ldcg(src + (size_t)c * (kS * kS) + o);
+    for (int o = blockIdx.x * nw + w; o < kS * kS; o += nb * nw) {
+        u64 s = 0;
+        for (int c = lane; c < nb; c += 32) s += __ldcg(src + (size_t)c * (kS * kS) + o);
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long tot = 0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += sm.red[i];
-            const int ai = o / kS, bi = o % kS;
-            if (ai < a.s && bi < a.s) a.S[(step * a.s + ai) * a.s + bi] = red64(tot, a.M);
-        }
-        __syncthreads();
+        const int ai = o / kS, bi = o % kS;
+        if (lane == 0 && ai < a.s && bi < a.s) a.S[(step * a.s + ai) * a.s + bi] = red64(s, a.M);
     }
 }
 
 __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_constant__ SeqArgs a)
 {
     __shared__ SeqSmem sm;
-    for (int t = threadIdx.x; t < kS * kS; t += blockDim.x) sm.acc[t] = 0;
+    if (threadIdx.x < kMaxEnt) sm.doff[threadIdx.x] = threadIdx.x < a.ndiag ? a.doff[threadIdx.x] : 0;
+    __syncthreads();
     const long long nb = gridDim.x;
-    const long long r0 = a.n * blockIdx.x / nb, r1 = a.n * (blockIdx.x + 1) / nb;
+    // 16-row aligned slices, so that every k-step covers one 16-row group
+    const int r0 = (int)(((a.n * blockIdx.x / nb) >> 4) << 4);
+    const int r1 = blockIdx.x + 1 == nb ? (int)a.n : (int)(((a.n * (blockIdx.x + 1) / nb) >> 4) << 4);
     if (a.nsteps <= 0 && !a.Vnext) return;
-    bool skip = a.test_skip && blockIdx.x == 0;
+    const bool skip = a.test_skip && blockIdx.x == 0;
+    u64 pacc[2][2][4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int e = 0; e < 4; ++e) pacc[i][j][e] = 0;
     // S_0 = X^T Y
     if (a.nsteps > 0) {
-        spmm_and_project(a, sm, a.V0, a.V0, r0, r1, false, true);
-        publish_partial(a, sm, 0);
+        spmm_and_project(a, sm, a.V0, a.V0, r0, r1, false, true, pacc);
+        publish_partial(a, sm, 0, pacc);
         if (!grid_barrier(a, skip)) return;
-        reduce_step(a, sm, 0, 0);
+        reduce_step(a, 0, 0);
     }
     long long done = 0;  // SpMMs done: V_done is current
     for (long long i = 0; i < a.nsteps; ++i) {
@@ -305,15 +324,15 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         const unsigned short *Vin = (i & 1) ? a.V1 : a.V0;
         unsigned short *Vout = (i & 1) ? a.V0 : a.V1;
         const bool proj = i + 1 < a.nsteps;
-        spmm_and_project(a, sm, Vin, Vout, r0, r1, true, proj);
-        if (proj) publish_partial(a, sm, (int)((i + 1) & 1));
+        spmm_and_project(a, sm, Vin, Vout, r0, r1, true, proj, pacc);
+        if (proj) publish_partial(a, sm, (int)((i + 1) & 1), pacc);
         if (!grid_barrier(a, false)) return;
         done = i + 1;
-        if (proj) reduce_step(a, sm, (int)((i + 1) & 1), i + 1);
+        if (proj) reduce_step(a, (int)((i + 1) & 1), i + 1);
     }
     if (a.Vnext) {
         const unsigned short *Vf = (done & 1) ? a.V1 : a.V0;
-        for (long long t = r0 * a.s + threadIdx.x; t < r1 * a.s; t += blockDim.x) {
+        for (long long t = (long long)r0 * a.s + threadIdx.x; t < (long long)r1 * a.s; t += blockDim.x) {
             const long long row = t / a.s;
             const int c = (int)(t - row * a.s);
             a.Vnext[t] = __ldcg(Vf + row * kS + c);
@@ -321,22 +340,46 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
     }
 }
 
-// X, Y (n x s, u32) -> Xh, V0 (n x 16, u16, zero padded, reduced mod p).
-__global__ void k_seq_prepare(long long n, int s, const u32 *__restrict__ X,
-                              const u32 *__restrict__ Y, unsigned short *Xh,
-                              unsigned short *V0, const Mod M)
+// Y (n x s, u32) -> V0 (n x 16, u16, zero padded, reduced mod p).
+__global__ void k_seq_prepare_v(long long n, int s, const u32 *__restrict__ Y,
+                                unsigned short *V0, const Mod M)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * kS) return;
     const long long row = t / kS;
     const int c = (int)(t - row * kS);
-    u32 xv = 0, yv = 0;
-    if (c < s) {
-        xv = red64(X[row * s + c], M);
-        yv = red64(Y[row * s + c], M);
-    }
-    Xh[t] = (unsigned short)xv;
-    V0[t] = (unsigned short)yv;
+    V0[t] = (unsigned short)(c < s ? red64(Y[row * s + c], M) : 0u);
+}
+
+// X (n x s, u32) -> its 8-bit limbs in m16n8k16 A-fragment order: for the
+// 16-row group q, limb l and lane (g = lane/4, t = lane%4) the four f16x2
+// words hold A[g][2t..2t+1], A[g+8][2t..2t+1], A[g][2t+8..9], A[g+8][2t+8..9]
+// with A[a][k] = limb l of X[16q + k][a] (rows past n are zero).
+__global__ void k_seq_prepare_x(long long n, int s, const u32 *__restrict__ X, uint4 *XF,
+                                const Mod M)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nq = (n + 15) / 16;
+    if (t >= nq * 2 * 32) return;
+    const int lane = (int)(t & 31);
+    const int l = (int)((t >> 5) & 1);
+    const long long q = t >> 6;
+    const int g = lane >> 2, tt = lane & 3;
+    auto limb = [&](int k, int col) -> u32 {
+        const long long row = q * 16 + k;
+        if (row >= n || col >= s) return 0u;
+        const u32 v = red64(X[row * s + col], M);
+        return l ? (v >> 8) & 255u : v & 255u;
+    };
+    auto pair = [&](int k, int col) -> u32 {
+        return bytes_to_half2(limb(k, col) | (limb(k + 1, col) << 16));
+    };
+    uint4 r;
+    r.x = pair(2 * tt, g);
+    r.y = pair(2 * tt, g + 8);
+    r.z = pair(2 * tt + 8, g);
+    r.w = pair(2 * tt + 8, g + 8);
+    XF[t] = r;
 }
 
 // ---------------------------------------------------------------------------
@@ -391,7 +434,8 @@ struct SeqState {
     // work buffers
     void *work = nullptr;
     size_t work_bytes = 0;
-    unsigned short *Xh = nullptr, *V0 = nullptr, *V1 = nullptr;
+    uint4 *XF = nullptr;
+    unsigned short *V0 = nullptr, *V1 = nullptr;
     u32 *partial = nullptr;
     unsigned *bar = nullptr;
     int nblocks = 0;
@@ -454,7 +498,8 @@ bool build_seq_layout(ffspmv_handle *h, SeqState &q)
         }
         width = std::max(width, rest[i]);
     }
-    if (width > 64) return false;  // one thread per row: keep rows short
+    if (width + (long long)diag.size() > kMaxEnt) return false;  // short rows only
+    if (n * kS >= (1LL << 31) || width * ld >= (1LL << 31)) return false;  // 32-bit indices
     std::vector<u32> ecol((size_t)(width * ld), 0), rownb(n);
     std::vector<unsigned short> eval((size_t)(width * ld), 0);
     bool uniform = true;
@@ -499,9 +544,11 @@ bool build_seq_layout(ffspmv_handle *h, SeqState &q)
 ffspmv_status ensure_work(SeqState &q, long long n, int nblocks)
 {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t nq = (size_t)((n + 15) / 16);
+    size_t xb = al(nq * 64 * sizeof(uint4));
     size_t vb = al((size_t)n * kS * 2 + 16);
     size_t pb = al((size_t)2 * nblocks * kS * kS * 4);
-    size_t need = 3 * vb + pb + 256;
+    size_t need = xb + 2 * vb + pb + 256;
     if (need > q.work_bytes) {
         if (q.work) cudaFree(q.work);
         q.work = nullptr;
@@ -510,11 +557,11 @@ ffspmv_status ensure_work(SeqState &q, long long n, int nblocks)
         q.work_bytes = need;
     }
     char *b = (char *)q.work;
-    q.Xh = (unsigned short *)b;
-    q.V0 = (unsigned short *)(b + vb);
-    q.V1 = (unsigned short *)(b + 2 * vb);
-    q.partial = (u32 *)(b + 3 * vb);
-    q.bar = (unsigned *)(b + 3 * vb + pb);
+    q.XF = (uint4 *)b;
+    q.V0 = (unsigned short *)(b + xb);
+    q.V1 = (unsigned short *)(b + xb + vb);
+    q.partial = (u32 *)(b + xb + 2 * vb);
+    q.bar = (unsigned *)(b + xb + 2 * vb + pb);
     q.nblocks = nblocks;
     return FFSPMV_OK;
 }
@@ -632,7 +679,7 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
     a.col = q->col;
     a.val = q->val;
     a.rownb = q->rownb;
-    a.Xh = q->Xh;
+    a.XF = q->XF;
     a.V0 = q->V0;
     a.V1 = q->V1;
     a.partial = q->partial;
@@ -653,7 +700,9 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
         cudaGraph_t g = nullptr;
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            k_seq_prepare<<<(unsigned)((n * kS + 255) / 256), 256, 0, cs>>>(n, s, d_X, d_Y, q->Xh, q->V0, a.M);
+            const long long nxf = (n + 15) / 16 * 64;
+            k_seq_prepare_x<<<(unsigned)((nxf + 255) / 256), 256, 0, cs>>>(n, s, d_X, q->XF, a.M);
+            k_seq_prepare_v<<<(unsigned)((n * kS + 255) / 256), 256, 0, cs>>>(n, s, d_Y, q->V0, a.M);
             cudaMemsetAsync(q->bar, 0, 2 * sizeof(unsigned), cs);
             cudaMemsetAsync(h->d_status, 0, sizeof(int), cs);
             cudaLaunchConfig_t cfg;

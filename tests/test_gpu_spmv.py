@@ -62,9 +62,36 @@ def test_powerlaw_medium(lib, fmt, use_pm1):
     # Zipf rows (mean 16, max 3000) with a ragged tail; several tiles per bin
     for m, pm in ((65521, 0.3), (2**31 - 1, 0.0), (3, 0.0)):
         A = gen.powerlaw_matrix(seed=7, n=30_011, lmax=3000, m=m, pm_fraction=pm)
+        if fmt == "DIA":
+            # ~60k occupied diagonals x 30k rows: refused by the size guard
+            with pytest.raises(lib.FFSPMVError) as e:
+                make(lib, A, fmt, use_pm1=use_pm1, guard_bytes=1 << 30)
+            assert e.value.status == 5
+            continue
         M = make(lib, A, fmt, use_pm1=use_pm1, guard_bytes=1 << 30)
         check_apply(lib, M, A, seed=11)
         check_apply(lib, M, A, transpose=True, alpha=5, beta=1, seed=12)
+
+
+@pytest.mark.parametrize("fmt", ["DIA", "HYBRID", "BINNED", "ELLR"])
+def test_banded_and_block_diagonal(lib, fmt):
+    for A in (gen.banded_matrix(4, 20_000, np.full(20_000, 12), 65521, pm_fraction=0.5),
+              gen.block_diagonal_matrix(5, 9_000, 300, np.full(9_000, 30), 2**31 - 1)):
+        M = make(lib, A, fmt, guard_bytes=1 << 30)
+        check_apply(lib, M, A, seed=1)
+        check_apply(lib, M, A, transpose=True, alpha=2, beta=3, seed=2)
+        check_apply(lib, M, A, nvec=4, seed=3)
+
+
+def test_split_long_rows(lib):
+    # rows far longer than one CTA chunk, in every plan that splits them
+    lengths = np.array([30_000, 1, 9000, 0, 4097, 4096, 4095, 70_000, 2], dtype=np.int64)
+    A = gen.uniform_matrix(3, lengths.size, 100_000, lengths, 2**31 - 1, pm_fraction=0.3)
+    for fmt in ("HYBRID", "BINNED", "COO", "CSR"):
+        for pm in (0, 1):
+            M = make(lib, A, fmt, use_pm1=pm)
+            check_apply(lib, M, A, alpha=3, beta=4, seed=pm)
+            check_apply(lib, M, A, nvec=3, seed=pm + 2)
 
 
 def test_rectangular_and_empty_rows(lib):
