@@ -158,6 +158,29 @@ ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
                                uint32_t *const *d_y, const int32_t *nvec,
                                ffspmv_stream_t stream);
 
+/*
+ * Y <- alpha*A^T*X + beta*Y (mod m), like spmv_apply_transpose with
+ * FFSPMV_TRANSPOSE_ATOMIC, but without allocating anything: for callers that
+ * cannot let a library call cudaMalloc or cudaFree while they run (a serving
+ * process whose device memory is all reserved up front for its own pool; a
+ * latency-bound caller that cannot take the implicit device-wide
+ * synchronisation of cudaFree).  The paper has no counterpart of this call.
+ * The exact per-column sums live in one fixed 8 MiB array of 2^20 64-bit
+ * words that every device which loads the library holds until the process
+ * exits; ncols * min(nvec, 16) must fit in it, so ncols <= 2^20 (larger
+ * ncols: FFSPMV_ERR_UNSUPPORTED; wider blocks are done 2^20/ncols vectors at
+ * a time).  h must have been created with FFSPMV_TRANSPOSE_ATOMIC (else
+ * FFSPMV_ERR_UNSUPPORTED).  The first call on a device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * each clears the part it uses: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and give wrong results.
+ */
+ffspmv_status spmv_apply_transpose_noalloc(ffspmv_t h, const uint32_t *d_x,
+                                           int64_t ldx, uint32_t *d_y, int64_t ldy,
+                                           int32_t nvec, uint32_t alpha, uint32_t beta,
+                                           ffspmv_stream_t stream);
+
 /* Free every device buffer of h.  NULL is accepted. */
 ffspmv_status spmv_destroy(ffspmv_t h);
 

@@ -73,6 +73,12 @@ def spmv_apply_transpose(h, x, ldx, y, ldy, nvec, alpha=1, beta=0, stream=None):
           "spmv_apply_transpose")
 
 
+def spmv_apply_transpose_noalloc(h, x, ldx, y, ldy, nvec, alpha=1, beta=0, stream=None):
+    check(lib().spmv_apply_transpose_noalloc(h, _ptr(x), int(ldx), _ptr(y), int(ldy), int(nvec),
+                                             int(alpha), int(beta), stream_ptr(stream)),
+          "spmv_apply_transpose_noalloc")
+
+
 def spmv_block_sequence(h, X, Y, s, nsteps, S, V_next=None, stream=None):
     check(lib().spmv_block_sequence(h, _ptr(X), _ptr(Y), int(s), int(nsteps), _ptr(S),
                                     _ptr(V_next), stream_ptr(stream)),
@@ -187,6 +193,7 @@ def to_numpy_u32(t):
 
 
 __all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
+           "spmv_apply_transpose_noalloc",
            "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
            "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "stream_ptr",
            "to_numpy_u32",

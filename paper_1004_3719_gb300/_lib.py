@@ -74,6 +74,8 @@ def _declare(L):
                                 ctypes.POINTER(_I64), ctypes.POINTER(_U32),
                                 ctypes.POINTER(_I64)]
     L.spmv_get_info.restype = ctypes.c_int
+    L.spmv_apply_transpose_noalloc.argtypes = [_P, _P, _I64, _P, _I64, _I32, _U32, _U32, _P]
+    L.spmv_apply_transpose_noalloc.restype = ctypes.c_int
     L.spmv_count_launches.argtypes = [_P, _I32, _I32, ctypes.POINTER(_I64)]
     L.spmv_count_launches.restype = ctypes.c_int
     for name, args, res in EXTRA_SIGNATURES:
