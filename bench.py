@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--extras", default="formats,sequence",
                     help="comma list from formats,sequence,batch ('' for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", default="",
+                    help="'ax' or 'atx': only run warm-up + --steps launches of that product "
+                         "(no timing, no extras), for an ncu capture")
     return ap.parse_args()
 
 
@@ -361,6 +364,16 @@ def main():
     def step():
         ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, sp)
         ff.spmv_apply_transpose(M.handle, x, 1, z, 1, 1, 1, 0, sp)
+
+    if args.profile:
+        fn = ff.spmv_apply if args.profile == "ax" else ff.spmv_apply_transpose
+        out = y if args.profile == "ax" else z
+        for _ in range(args.warmup + args.steps):
+            fn(M.handle, x, 1, out, 1, 1, 1, 0, sp)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "launches": M.launches(args.profile == "atx", 1),
+                          "plan": M.describe().splitlines()[0]}))
+        return
 
     for _ in range(max(args.warmup, 3)):
         step()

@@ -47,11 +47,11 @@ typedef enum {
 enum {
     FFSPMV_FMT_AUTO = 0,
     FFSPMV_FMT_CSR = 1,     /* plain CSR, one fixed thread-group width per row */
-    FFSPMV_FMT_ELLR = 2,    /* ELL_R: column-major ELL + per-row counts (Sec. 2.4.4) */
+    FFSPMV_FMT_ELLR = 2,    /* ELL_R: column-major ELL + per-row counts (Sec. 2.4.3) */
     FFSPMV_FMT_COO = 3,     /* coordinate triples, element-parallel segmented sums */
-    FFSPMV_FMT_COOS = 4,    /* COO_S: CSR over the non-empty rows only (Sec. 2.4.5) */
+    FFSPMV_FMT_COOS = 4,    /* COO_S: CSR over the non-empty rows only (Sec. 2.4.4) */
     FFSPMV_FMT_DIA = 5,     /* diagonals + offsets; refused past a size guard */
-    FFSPMV_FMT_HYBRID = 6,  /* paper heuristic: DIA + ELL_R(w) + CSR/COO/COO_S residue (Sec. 2.4.6) */
+    FFSPMV_FMT_HYBRID = 6,  /* paper heuristic: DIA + ELL_R(w) + CSR/COO/COO_S residue (Sec. 2.4.5) */
     FFSPMV_FMT_BINNED = 7   /* rows binned by length, one format per bin */
 };
 
@@ -98,7 +98,7 @@ void ffspmv_options_default(ffspmv_options *opt);
  * device memory; they are copied and may be freed on return.
  * modulus: 2 <= m <= 2^32 - 1.  opt: NULL = defaults.  The call is
  * synchronous (it returns once the plan is resident on the current device).
- * Format choice follows Sec. 2.4.6 (hybridisation and the heuristic chooser)
+ * Format choice follows Sec. 2.4.4-2.4.5 (hybridisation and the heuristic chooser)
  * or the selector named in opt.  On error *out is NULL and nothing leaks.
  */
 ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,

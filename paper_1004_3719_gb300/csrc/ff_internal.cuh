@@ -107,7 +107,7 @@ struct AccWide {
 // Plan segments.  A plan is a list of segments; each covers a set of rows
 // (or of entries, for COO) in one storage format.  Segments of one phase own
 // disjoint rows and run in one launch; phase 2 segments add into rows that a
-// phase 1 segment has already written (the column split of Sec. 2.4.5).
+// phase 1 segment has already written (the column split of Sec. 2.4.4, Hybridization).
 enum SegKind : int {
     SEG_CSR = 0,     // `group` lanes per row
     SEG_CSRBLK = 1,  // one CTA per row

@@ -251,7 +251,7 @@ __device__ void seg_csrsplit(const SegDesc &S, long long lb, const u32 *__restri
 
 // ---------------------------------------------------------------------------
 // One thread per row: DIA diagonals, then ELL_R columns (column-major, Sec.
-// 2.1; coalesced on the GPU, Sec. 2.4.4).
+// 2.1; coalesced on the GPU, Sec. 2.4.3).
 template <class Acc, int NV>
 __device__ void seg_ellr(const SegDesc &S, long long lb, const u32 *__restrict__ x,
                          long long ldx, u32 *__restrict__ y, long long ldy,

@@ -2,11 +2,11 @@
 // of Sec. 2.1 and 2.4 and lay every part out for the device.
 //
 //   CSR     plain row-wise storage, `group` lanes per row
-//   ELLR    ELL_R, column-major with per-row counts (Sec. 2.4.4)
+//   ELLR    ELL_R, column-major with per-row counts (Sec. 2.4.3, Basic formats)
 //   COO     coordinate triples (Sec. 2.1), element-parallel
-//   COOS    COO_S: CSR over the non-empty rows only (Sec. 2.4.5)
+//   COOS    COO_S: CSR over the non-empty rows only (Sec. 2.4.4, Hybridization)
 //   DIA     diagonals stored densely with their offsets (Sec. 2.1)
-//   HYBRID  the heuristic chooser of Sec. 2.4.6: dense diagonals to DIA, the
+//   HYBRID  the heuristic chooser of Sec. 2.4.5: dense diagonals to DIA, the
 //           first w entries of every row to ELL_R, the residue to CSR, COO or
 //           COO_S by its number of non-empty rows and entries per row
 //   BINNED  rows binned by length, one format per bin (the library's own
@@ -715,7 +715,7 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
         break;
     }
     case FFSPMV_FMT_HYBRID: {
-        // Sec. 2.4.6: DIA for dense diagonals; if the matrix is large enough
+        // Sec. 2.4.5: DIA for dense diagonals; if the matrix is large enough
         // and most rows are filled, an ELL_R part of width w; the residue to
         // CSR, COO or COO_S by its empty rows and entries per row.
         name = "HYBRID";

@@ -4,7 +4,7 @@
 // Persistent path (p <= 2^16, s <= 16, A square and splittable into a few
 // dense diagonals plus a narrow ELL_R part): one cooperative kernel runs every
 // step.  CTA c owns a contiguous slice of rows; per step it forms its rows of
-// V_{i+1} = A V_i (DIA + ELL_R, Sec. 2.4.5), stores them, and projects them on
+// V_{i+1} = A V_i (DIA + ELL_R, Sec. 2.4.4), stores them, and projects them on
 // the matching rows of X with tensor-core MMAs on 8-bit limbs; a bounded grid
 // barrier then publishes V_{i+1} and the per-CTA partial projections, which
 // the CTAs sum into S_{i+1}.  The kernel is captured in a CUDA graph.
