@@ -43,7 +43,8 @@ typedef enum {
     FFSPMV_ERR_TIMEOUT = 6      /* a bounded device wait expired (grid barrier) */
 } ffspmv_status;
 
-/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO lets the selector choose. */
+/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO is the binned layout with
+ * the bin formats picked by opt.selector. */
 enum {
     FFSPMV_FMT_AUTO = 0,
     FFSPMV_FMT_CSR = 1,     /* plain CSR, one fixed thread-group width per row */

@@ -85,8 +85,34 @@ def _declare(L):
             fn.restype = res
 
 
-# Entry points declared in include/ffspmv_select.h and include/ffspmv_batch.h.
-EXTRA_SIGNATURES = []
+_F = ctypes.c_float
+# Entry points declared in include/ffspmv_select.h.
+EXTRA_SIGNATURES = [
+    ("ffspmv_matrix_features", [_I64, _I64, _P, _P, _P, _U32, _P, _P, _P], ctypes.c_int),
+    ("ffspmv_tune_bins", [_I64, _I64, _I64, _P, _P, _P, _U32, _I32, _I64, _I32, _P, _P, _P, _P],
+     ctypes.c_int),
+    ("ffspmv_mlp_forward", [_P, _P, _I32, _P, _P, _P], ctypes.c_int),
+    ("ffspmv_mlp_loss", [_P, _P, _P, _I32, _P, _P, _P], ctypes.c_int),
+    ("ffspmv_mlp_backward", [_P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    ("ffspmv_mlp_adam", [_P, _P, _P, _P, _I32, _F, _F, _F, _F, _P], ctypes.c_int),
+    ("ffspmv_selector_load", [_P, _I64], ctypes.c_int),
+    ("ffspmv_heuristic_choose", [_I64, _P, _P, _U32, _I32, _P], ctypes.c_int),
+    ("ffspmv_selector_choose", [_I64, _I64, _I64, _P, _P, _P, _U32, _P], ctypes.c_int),
+    ("spmv_create_binned", [ctypes.POINTER(_P), _I64, _I64, _I64, _P, _P, _P, _U32, _P,
+                            ctypes.POINTER(Options), _P], ctypes.c_int),
+]
+
+# Sizes of the selector network (include/ffspmv_select.h).
+NUM_BINS = 17
+NUM_FORMATS = 10
+NUM_FEATURES = 16
+NUM_BIN_FEATURES = 6
+MLP_IN = NUM_FEATURES + NUM_BIN_FEATURES
+MLP_HIDDEN = 64
+MLP_OUT = NUM_FORMATS + 1
+MLP_PARAMS = (MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN
+              + MLP_OUT * MLP_HIDDEN + MLP_OUT)
+SELECTOR_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.npy")
 
 
 def lib():
@@ -100,7 +126,19 @@ def lib():
         L = ctypes.CDLL(path)
         _declare(L)
         _lib_handle = L
+        _install_default_selector(L)
     return _lib_handle
+
+
+def _install_default_selector(L):
+    """Install the committed selector weights (written by train_selector.py)
+    for FFSPMV_SEL_LEARNED, if the file exists."""
+    if not os.path.exists(SELECTOR_WEIGHTS):
+        return
+    import numpy as np
+    w = np.ascontiguousarray(np.load(SELECTOR_WEIGHTS), dtype=np.float32)
+    if w.size == MLP_PARAMS:
+        L.ffspmv_selector_load(w.ctypes.data, w.size)
 
 
 def status_string(s):

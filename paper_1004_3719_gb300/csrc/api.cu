@@ -6,6 +6,7 @@
 #include "ff_internal.cuh"
 #include "ff_plan.h"
 #include "ff_select.h"
+#include "../../include/ffspmv_select.h"
 
 using namespace ff;
 
@@ -68,7 +69,7 @@ ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
         return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, bins);
     }
     ffspmv_options o2 = o;
-    if (o2.priority_format == FFSPMV_FMT_AUTO) o2.priority_format = FFSPMV_FMT_HYBRID;
+    if (o2.priority_format == FFSPMV_FMT_AUTO) o2.priority_format = FFSPMV_FMT_BINNED;
     return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, nullptr);
 }
 
@@ -244,6 +245,40 @@ ffspmv_status spmv_apply_transpose(ffspmv_t h, const uint32_t *d_x, int64_t ldx,
                                    uint32_t alpha, uint32_t beta, ffspmv_stream_t stream)
 {
     return apply_common(h, true, d_x, ldx, d_y, ldy, nvec, alpha, beta, stream);
+}
+
+ffspmv_status spmv_create_binned(ffspmv_t *out, int64_t nrows, int64_t ncols, int64_t nnz,
+                                 const int64_t *row_ptr, const int32_t *col, const uint32_t *values,
+                                 uint32_t modulus, const int32_t *best, const ffspmv_options *opt,
+                                 ffspmv_stream_t stream)
+{
+    if (!out || !best) return FFSPMV_ERR_ARG;
+    *out = nullptr;
+    ffspmv_options o;
+    ffspmv_options_default(&o);
+    if (opt) o = *opt;
+    // build through the normal path with the heuristic table, then rebuild A's
+    // plan with the given bins (A^T keeps the options' selector)
+    ffspmv_options o2 = o;
+    o2.priority_format = FFSPMV_FMT_BINNED;
+    o2.selector = FFSPMV_SEL_HEURISTIC;
+    ffspmv_status st = spmv_create_hybrid(out, nrows, ncols, nnz, row_ptr, col, values, modulus, &o2, stream);
+    if (st != FFSPMV_OK) return st;
+    ffspmv_handle *h = *out;
+    BinChoice bins[kBins];
+    for (int b = 0; b < kBins; ++b) {
+        const int f = best[3 * b], pm = best[3 * b + 1], valid = best[3 * b + 2];
+        bins[b] = (valid && f >= 0 && f < kFormats) ? format_choice(f, pm ? 1 : 0)
+                                                   : heuristic_bin_choice(b, 0.0, o.use_pm1);
+    }
+    free_plan(h->A);
+    h->A = Plan();
+    st = build_plan_ex(h->A, nrows, ncols, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), modulus, o2, bins);
+    if (st != FFSPMV_OK) {
+        destroy_handle(h);
+        *out = nullptr;
+    }
+    return st;
 }
 
 ffspmv_status spmv_destroy(ffspmv_t h)

@@ -26,6 +26,19 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                             const long long *ptr, const int *col, const u32 *val,
                             u32 m, const ffspmv_options &opt, const BinChoice *bins);
 
+// Sub-plans over a subset of rows (the exhaustive search).
+struct PlanSource;
+PlanSource *make_source(long long nrows, long long ncols, const long long *ptr, const int *col,
+                        const u32 *val, u32 m);
+void free_source(PlanSource *s);
+ffspmv_status build_rows_plan(Plan &P, const PlanSource &src, const std::vector<u32> &rows,
+                              const BinChoice &c);
+
+// The candidate formats of a bin (index f of ffspmv_select.h) and their validity.
+constexpr int kFormats = 10;
+BinChoice format_choice(int f, int pm);
+bool format_valid(int f, int bin, long long maxlen);
+
 void transpose_csr(long long nrows, long long ncols, const long long *ptr,
                    const int *col, const u32 *val, std::vector<long long> &tptr,
                    std::vector<int> &tcol, std::vector<u32> &tval);

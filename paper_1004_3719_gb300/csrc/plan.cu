@@ -650,7 +650,7 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
     const long long guard = opt.guard_bytes > 0 ? opt.guard_bytes : (32LL << 30);
     const int upm = opt.use_pm1;
     int fmt = opt.priority_format;
-    if (fmt == FFSPMV_FMT_AUTO) fmt = bins ? FFSPMV_FMT_BINNED : FFSPMV_FMT_HYBRID;
+    if (fmt == FFSPMV_FMT_AUTO) fmt = FFSPMV_FMT_BINNED;
     P.format = fmt;
     Blob B;
     std::vector<std::vector<SegBuild>> phases(1);
@@ -829,6 +829,66 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
     if (st != FFSPMV_OK) return st;
     describe(P, name);
     return FFSPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sub-plans over a row subset, for the exhaustive search.
+struct PlanSource {
+    Mat A;
+    u32 m;
+};
+
+PlanSource *make_source(long long nrows, long long ncols, const long long *ptr, const int *col,
+                        const u32 *val, u32 m)
+{
+    PlanSource *s = new PlanSource();
+    s->A = load_matrix(nrows, ncols, ptr, col, val, m);
+    s->m = m;
+    return s;
+}
+
+void free_source(PlanSource *s) { delete s; }
+
+ffspmv_status build_rows_plan(Plan &P, const PlanSource &src, const std::vector<u32> &rows,
+                              const BinChoice &c)
+{
+    const Mat &A = src.A;
+    P.nrows = A.nrows;
+    P.ncols = A.ncols;
+    P.nnz = 0;
+    long long maxlen = 0;
+    for (u32 i : rows) {
+        long long L = A.ptr[i + 1] - A.ptr[i];
+        maxlen = std::max(maxlen, L);
+        P.nnz += L;
+    }
+    {
+        const u32 m = src.m;
+        unsigned __int128 B = (unsigned __int128)(m - 1) * (m - 1);
+        if (B < m) B = m;
+        unsigned __int128 kmax = (~(unsigned __int128)0 >> 64) / B;
+        P.acc_wide = (unsigned __int128)maxlen > kmax ? 1 : 0;
+    }
+    Rows R;
+    R.ids = rows;
+    R.n = (long long)rows.size();
+    Blob B;
+    std::vector<std::vector<SegBuild>> phases(1);
+    SegBuild s;
+    bool ok;
+    const int pm = c.pm ? 1 : 0;
+    if (c.kind == SEG_ELLR)
+        ok = make_ellr(B, A, R, {}, nullptr, pm, 0, src.m, 1LL << 32, s);
+    else if (c.kind == SEG_COO)
+        ok = make_coo(B, A, R, pm, 0, src.m, s);
+    else if (c.kind == SEG_CSRSPLIT)
+        ok = make_csrsplit(B, A, R, pm, 0, src.m, s);
+    else
+        ok = make_csr(B, A, R, c.kind == SEG_CSRBLK ? SEG_CSRBLK : SEG_CSR,
+                      std::max(1, std::min(32, c.group)), pm, 0, src.m, s);
+    if (!ok) return FFSPMV_ERR_UNSUPPORTED;
+    phases[0].push_back(s);
+    return finish(P, B, phases);
 }
 
 ffspmv_status build_plan(Plan &P, long long nrows, long long ncols,

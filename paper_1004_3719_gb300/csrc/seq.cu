@@ -33,7 +33,6 @@ constexpr int kS = 16;                            // block width of the persiste
 constexpr int kCPT = 8;                           // components per thread
 constexpr int kTPR = kS / kCPT;                   // threads per row
 constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 256
-constexpr int kKSteps = kRowsPerPass / 16;        // 16 k-steps of 16 rows
 constexpr int kMaxEnt = 16;                       // DIA + ELL_R entries per row
 constexpr int kVsStride = 20;                     // halves per staged row (no bank conflicts)
 constexpr unsigned kDefaultSpins = 1u << 22;      // x <= 64 ns sleeps: well under a second

@@ -1,0 +1,146 @@
+"""GPU tests of the format selector: the feature kernel and the network's
+forward / loss / backward / Adam kernels against the fp64 CPU oracle, the
+exhaustive search, bit-exact results of every selected plan, and what the
+trained network gains over the heuristic table on held-out matrices."""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import rand_block, to_dev, to_host
+from oracle import features as F
+from oracle import mlp as OM
+
+pytestmark = pytest.mark.gpu
+
+
+def _matrices():
+    return [gen.tiny_matrix(),
+            gen.powerlaw_matrix(seed=3, n=40_000, lmax=5000, m=3),
+            gen.wiedemann_matrix(seed=4, n=20_000),
+            gen.banded_matrix(5, 30_000, np.full(30_000, 9), 2**31 - 1, pm_fraction=0.6),
+            gen.block_diagonal_matrix(6, 20_000, 200, np.full(20_000, 25), 65521),
+            gen.random_small(7, 900, 300, 0.02, 27, pm_fraction=0.3)]
+
+
+def test_feature_kernel_matches_oracle(lib):
+    from paper_1004_3719_gb300 import selector as sel
+    for A in _matrices():
+        f, g = sel.matrix_features(A)
+        fo, go = F.features(A.nrows, A.ncols, A.row_ptr, A.col, A.val, A.modulus)
+        assert np.allclose(f, fo, rtol=1e-5, atol=1e-6), (A.name, f, fo)
+        assert np.allclose(g, go, rtol=1e-5, atol=1e-6), A.name
+
+
+def _batch(seed, B=300):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 1, (B, OM.IN)).astype(np.float32)
+    t = rng.normal(0, 1, (B, OM.OUT)).astype(np.float32)
+    mk = (rng.random((B, OM.OUT)) < 0.6).astype(np.float32)
+    return x, t, mk
+
+
+def test_mlp_kernels_match_oracle(lib):
+    import torch
+    from paper_1004_3719_gb300 import selector as sel
+    p = sel.init_params(3)
+    p[OM.H * OM.IN:OM.H * OM.IN + OM.H] = 0.05        # non-zero biases
+    net = sel.MLP(params=p)
+    x, t, mk = _batch(4)
+    X, T, MK = (torch.from_numpy(a).cuda() for a in (x, t, mk))
+    out, _ = net.forward(X)
+    want, cache = OM.forward(p.astype(np.float64), x)
+    assert np.allclose(out.cpu().numpy(), want, rtol=1e-4, atol=1e-4)
+    loss, g = net.loss_and_grad(X, T, MK)
+    L, dout = OM.loss(want, t, mk)
+    gw = OM.backward(p.astype(np.float64), cache, dout)
+    assert np.isclose(loss.item(), L, rtol=1e-4)
+    assert np.allclose(g.cpu().numpy(), gw, rtol=1e-3, atol=1e-5)
+    # Adam step against the oracle's
+    net.adam(lr=1e-2)
+    p1, _, _ = OM.adam_step(p.astype(np.float64), gw, np.zeros(p.size), np.zeros(p.size), 1, 1e-2)
+    assert np.allclose(net.params(), p1, rtol=1e-4, atol=1e-5)
+
+
+def test_training_lowers_the_loss(lib):
+    import torch
+    from paper_1004_3719_gb300 import selector as sel
+    rng = np.random.default_rng(9)
+    x = rng.normal(0, 1, (2048, OM.IN)).astype(np.float32)
+    w = rng.normal(0, 1, (OM.IN, OM.OUT))
+    t = np.tanh(x @ w).astype(np.float32)          # a learnable target
+    mk = np.ones_like(t)
+    X, T, MK = (torch.from_numpy(a).cuda() for a in (x, t, mk))
+    net = sel.MLP(seed=1)
+    first = None
+    for step in range(400):
+        loss, _ = net.loss_and_grad(X, T, MK)
+        first = first if first is not None else loss.item()
+        net.adam(lr=3e-3)
+    assert loss.item() < 0.2 * first
+
+
+def test_exhaustive_search_and_exact_plans(lib):
+    from paper_1004_3719_gb300 import selector as sel
+    for A in _matrices()[:5]:
+        tune = sel.tune_bins(A, max_rows=4096, max_nnz=1 << 18, reps=2)
+        best = tune["best"]
+        L = np.diff(A.row_ptr)
+        nonempty = {int(b) for b in F.bin_of_length(L[L > 0])}
+        assert {b for b in range(1, 17) if best[b][2]} == nonempty
+        for b in nonempty:
+            assert np.isfinite(tune["times"][b][best[b][0]])
+        for choice in (best, sel.heuristic_choose(A)):
+            M = sel.create_binned(A, choice)
+            x = rand_block(1, A.ncols, 1, A.modulus)
+            y = to_host(M.apply(to_dev(x)))
+            assert np.array_equal(y, oracle.csr_spmv(A, x)), A.name
+
+
+def test_every_format_of_every_bin_is_exact(lib):
+    # all ten candidate formats, with and without +-1 segregation, on a matrix
+    # with rows in many bins
+    from paper_1004_3719_gb300 import selector as sel
+    lengths = np.concatenate([np.full(300, 1), np.full(200, 3), np.full(100, 20),
+                              np.full(30, 100), np.full(5, 700), [3000]])
+    rng = np.random.default_rng(2)
+    lengths = rng.permutation(lengths)
+    A = gen.uniform_matrix(8, lengths.size, 5000, lengths, 2**31 - 1, pm_fraction=0.4)
+    x = rand_block(3, A.ncols, 1, A.modulus)
+    want = oracle.csr_spmv(A, x)
+    for f in range(10):
+        for pm in (0, 1):
+            best = np.zeros((17, 3), dtype=np.int32)
+            best[1:, 0] = f
+            best[1:, 1] = pm
+            best[1:, 2] = 1
+            M = sel.create_binned(A, best)
+            assert np.array_equal(to_host(M.apply(to_dev(x))), want), (f, pm)
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1004_3719_gb300", "selector_weights.npy")
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained selector weights committed")
+def test_learned_selector_exact_and_better_than_heuristic(lib):
+    """Held-out matrices (indices beyond the training corpus): the learned
+    plans are bit-exact, and under the exhaustive search's own timings their
+    cost is no worse than the heuristic table's on average."""
+    from paper_1004_3719_gb300 import selector as sel
+    from paper_1004_3719_gb300.train_selector import best_cost, bin_nnz, choice_cost
+    ratios_l, ratios_h = [], []
+    for idx in range(50_000, 50_006):
+        A = gen.selector_matrix(1005, idx, rows_hi=200_000)
+        learned = sel.selector_choose(A)
+        M = lib.Matrix.from_csr(A, selector=lib.SEL.LEARNED, transpose_mode=lib.TRANSPOSE.NONE)
+        x = rand_block(idx, A.ncols, 1, A.modulus)
+        assert np.array_equal(to_host(M.apply(to_dev(x))), oracle.csr_spmv(A, x)), A.name
+        tune = sel.tune_bins(A)
+        nb = bin_nnz(A)
+        b = best_cost(tune, nb)
+        ratios_l.append(b / choice_cost(tune, nb, learned))
+        ratios_h.append(b / choice_cost(tune, nb, sel.heuristic_choose(A)))
+    assert np.mean(ratios_l) >= np.mean(ratios_h) - 0.02, (ratios_l, ratios_h)
