@@ -172,6 +172,22 @@ def cpu_baseline(A, x, seconds):
             "sample": f"{n} steps (y=A*x, z=A^T*x) on the full matrix, single thread, {dt:.1f} s"}
 
 
+def shard(count, rank, world):
+    """The units of `rank` when `count` independent units (problems, replicas)
+    are split over `world` ranks, round robin; no data moves between ranks."""
+    return list(range(rank, count, world))
+
+
+def max_over_ranks(dist, value, device="cpu"):
+    """Largest `value` over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,7 +261,8 @@ def timed_steps(torch, fn, steps, flush, stream):
 def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
     sp = stream.cuda_stream
     out = {}
-    fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED"]
+    fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED", "LEARNED", "EXHAUSTIVE"]
+    sel_of = {"LEARNED": ff.SEL.LEARNED, "EXHAUSTIVE": ff.SEL.EXHAUSTIVE}
     for m in moduli:
         A = gen.powerlaw_matrix(seed=SEED, m=m)
         x = torch.from_numpy(gen.uniform_block(SEED, A.ncols, 1, m).view(np.int32)).cuda()
@@ -255,8 +272,12 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
             for pm in ((0, 1) if m == 3 else (-1,)):
                 key = f if pm < 0 else f"{f}{'+pm1' if pm else '-nopm1'}"
                 try:
-                    M = ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, f),
-                                           transpose_mode=ff.TRANSPOSE.NONE, use_pm1=pm)
+                    if f in sel_of:
+                        M = ff.Matrix.from_csr(A, selector=sel_of[f], transpose_mode=ff.TRANSPOSE.NONE,
+                                               use_pm1=pm)
+                    else:
+                        M = ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, f),
+                                               transpose_mode=ff.TRANSPOSE.NONE, use_pm1=pm)
                 except ff.FFSPMVError as e:
                     row[key] = f"n/a ({e.status == 5 and 'size guard' or e})"
                     continue
@@ -400,11 +421,7 @@ def main():
     clk = clocks.stop()
     t_step = [e[0].elapsed_time(e[2]) for e in evs]
     t_ax = [e[0].elapsed_time(e[1]) for e in evs]
-    total_ms = sum(t_step)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, sum(t_step), "cuda")
     units = 2 * A.nnz * args.steps * world
     value = units / (total_ms / 1e3) / 1e9
     launches = args.steps * (M.launches(False, 1) + M.launches(True, 1))

@@ -351,7 +351,7 @@ def batch_problems(seed=1004, count=256, rows_lo=1_000, rows_hi=200_000,
         sub = int(rng.integers(0, 2**31))
         lrng = rng_for(sub, 9)
         if kind == "uniform":
-            lengths = lrng.integers(len_lo, len_hi + 1, n)
+            lengths = np.minimum(lrng.integers(len_lo, len_hi + 1, n), n)
             A = uniform_matrix(sub, n, n, lengths, p, name=f"b{j}-uniform")
         elif kind == "banded":
             lengths = lrng.integers(len_lo, len_hi + 1, n)

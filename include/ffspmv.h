@@ -152,7 +152,10 @@ ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X,
  * modulus); d_x / d_y: host arrays of device pointers, X_j: ncols_j x nvec[j]
  * row-major (ld = nvec[j]), Y_j: nrows_j x nvec[j]; 1 <= nvec[j] <= 32.
  * The work list is rebuilt on the host only when the set of handles or nvec
- * changes.
+ * changes; that first call also times a few tile shapes (rows per work item,
+ * length from which a row gets a whole CTA) on the device and keeps the
+ * fastest, writing the outputs several times with the same values.  Not
+ * thread-safe: one host thread at a time.
  */
 ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
                                const uint32_t *const *d_x,

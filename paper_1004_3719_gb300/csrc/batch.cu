@@ -1,12 +1,19 @@
 // Many independent products Y_j = A_j X_j (mod m_j) in one launch.
 //
-// The work list holds one item per tile of rows of one matrix.  A CTA runs one
-// item: a group of G lanes (G = the matrix's block width rounded up to a power
-// of two) handles one row, lane v accumulating component v of the row, so the
-// x loads of an entry are contiguous across the group and no cross-lane
-// reduction is needed.  Each matrix brings its own modulus and Barrett
-// constants (Sec. 2.2).  Items are ordered by decreasing estimated cost so
-// that the longest tiles start first.
+// The work list holds items of two kinds:
+//   rows     a tile of consecutive short rows of one matrix; a group of G
+//            lanes (G = the matrix's block width rounded up to a power of two)
+//            handles one row, lane v accumulating component v, so the x loads
+//            of an entry are contiguous across the group and need no
+//            cross-lane reduction;
+//   long row one row with at least `long_at` entries; the whole CTA shares
+//            its entries (256/G entry lanes x G component lanes) and sums the
+//            partials in shared memory.
+// Each matrix brings its own modulus and Barrett constants (Sec. 2.2).  Items
+// are ordered by decreasing estimated cost so that the longest start first.
+// The tile height and the long-row threshold are picked by timing: the first
+// call for a new set of handles and block widths tries a few shapes and
+// keeps the fastest.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -19,7 +26,6 @@ namespace ff {
 namespace {
 
 constexpr int kBatchThreads = 256;
-
 constexpr int kMaxBatch = 512;  // matrices per launch (pointer table in the launch parameters)
 
 struct BMat {
@@ -34,7 +40,7 @@ struct BMat {
 
 struct BItem {
     int mat;
-    int rows;        // rows in this item
+    int rows;        // rows in this item; 0 marks a long-row item
     long long row0;
 };
 
@@ -47,6 +53,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0,
         const __grid_constant__ BPtrs P)
 {
+    __shared__ u64 red[kBatchThreads];
     const BItem it = items[blockIdx.x];
     const BMat &A = mats[it.mat];
     const u32 *__restrict__ x = P.x[it.mat - mat0];
@@ -56,21 +63,56 @@ k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0
     const int grp = threadIdx.x / G;
     const int groups = kBatchThreads / G;
     const bool active_lane = lane < A.nvec;
-    for (int r = grp; r < it.rows; r += groups) {
-        const long long row = it.row0 + r;
-        const long long s = __ldg(A.ptr + row), e = __ldg(A.ptr + row + 1);
-        AccWide acc;
-        acc.zero();
-        if (active_lane) {
-            for (long long k = s; k < e; ++k) {
-                const long long c = __ldg(A.col + k);
-                const u32 a = __ldg(A.val + k);
-                acc.mad(a, __ldg(x + c * A.nvec + lane));
+    if (it.rows > 0) {
+        for (int r = grp; r < it.rows; r += groups) {
+            const long long row = it.row0 + r;
+            const long long s = __ldg(A.ptr + row), e = __ldg(A.ptr + row + 1);
+            AccWide acc;
+            acc.zero();
+            if (active_lane) {
+                for (long long k = s; k < e; ++k) {
+                    const long long c = __ldg(A.col + k);
+                    const u32 a = __ldg(A.val + k);
+                    acc.mad(a, __ldg(x + c * A.nvec + lane));
+                }
+                y[row * A.nvec + lane] = (u32)acc.partial(A.M);
             }
-            y[row * A.nvec + lane] = (u32)acc.partial(A.M);
+        }
+        return;
+    }
+    // one long row shared by the whole CTA
+    const long long row = it.row0;
+    const long long s = __ldg(A.ptr + row), e = __ldg(A.ptr + row + 1);
+    AccWide acc;
+    acc.zero();
+    if (active_lane) {
+        for (long long k = s + grp; k < e; k += groups) {
+            const long long c = __ldg(A.col + k);
+            const u32 a = __ldg(A.val + k);
+            acc.mad(a, __ldg(x + c * A.nvec + lane));
         }
     }
+    red[threadIdx.x] = active_lane ? acc.partial(A.M) : 0;  // each below m
+    __syncthreads();
+    for (int half = groups >> 1; half > 0; half >>= 1) {
+        if (grp < half) red[threadIdx.x] += red[threadIdx.x + half * G];
+        __syncthreads();
+    }
+    if (grp == 0 && active_lane) y[row * A.nvec + lane] = red64(red[threadIdx.x], A.M);
 }
+
+struct Shape {
+    int tile_mult;     // rows per item = tile_mult * (256 / G)
+    long long long_at; // rows with at least this many entries get a CTA
+};
+
+const Shape kShapes[] = {{1, 256}, {1, 1024}, {1, 1LL << 40}, {2, 256}, {2, 1024}, {4, 512}};
+constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+
+struct WorkList {
+    std::vector<BItem> items;
+    std::vector<int> chunk_item0;  // first item of each chunk of kMaxBatch matrices
+};
 
 struct BatchCache {
     std::vector<ffspmv_handle *> hs;
@@ -81,7 +123,8 @@ struct BatchCache {
     BMat *d_mats = nullptr;
     BItem *d_items = nullptr;
     int nitems = 0;
-    std::vector<int> chunk_item0;  // first item of each chunk of kMaxBatch matrices
+    std::vector<int> chunk_item0;
+    int shape = -1;
 };
 
 BatchCache g_cache;
@@ -115,6 +158,101 @@ int pow2_ceil(int v)
     return g;
 }
 
+// Items for one shape, each chunk of kMaxBatch matrices ordered by cost.
+WorkList make_items(const std::vector<ffspmv_handle *> &hs, const std::vector<BMat> &mats,
+                    const Shape &sh)
+{
+    WorkList W;
+    std::vector<std::pair<double, BItem>> items;
+    size_t chunk_begin = 0;
+    const int count = (int)hs.size();
+    auto sort_chunk = [&]() {
+        std::stable_sort(items.begin() + chunk_begin, items.end(),
+                         [](const auto &a, const auto &b) { return a.first > b.first; });
+    };
+    for (int j = 0; j < count; ++j) {
+        if (j % kMaxBatch == 0) {
+            sort_chunk();
+            chunk_begin = items.size();
+            W.chunk_item0.push_back((int)items.size());
+        }
+        const BMat &b = mats[j];
+        const long long tile = (long long)sh.tile_mult * (kBatchThreads / b.G);
+        const long long *p = hs[j]->h_ptr.data();
+        long long r0 = 0;
+        while (r0 < b.nrows) {
+            const long long L0 = p[r0 + 1] - p[r0];
+            if (L0 >= sh.long_at) {
+                BItem it;
+                it.mat = j;
+                it.row0 = r0;
+                it.rows = 0;
+                items.push_back({(double)L0 / (kBatchThreads / b.G), it});
+                ++r0;
+                continue;
+            }
+            long long r1 = r0;
+            double cost = 0;
+            while (r1 < b.nrows && r1 - r0 < tile && p[r1 + 1] - p[r1] < sh.long_at) {
+                cost = std::max(cost, (double)(p[r1 + 1] - p[r1]));
+                ++r1;
+            }
+            BItem it;
+            it.mat = j;
+            it.row0 = r0;
+            it.rows = (int)(r1 - r0);
+            items.push_back({cost * sh.tile_mult, it});
+            r0 = r1;
+        }
+    }
+    sort_chunk();
+    W.chunk_item0.push_back((int)items.size());
+    W.items.resize(items.size());
+    for (size_t i = 0; i < items.size(); ++i) W.items[i] = items[i].second;
+    return W;
+}
+
+ffspmv_status upload_items(BatchCache &C, const WorkList &W, int count)
+{
+    const size_t bm = (sizeof(BMat) * count + 255) / 256 * 256;
+    const size_t need = bm + sizeof(BItem) * std::max<size_t>(W.items.size(), 1) + 256;
+    if (need > C.dev_bytes) {
+        if (C.dev) cudaFree(C.dev);
+        C.dev = nullptr;
+        C.dev_bytes = 0;
+        if (cudaMalloc(&C.dev, need) != cudaSuccess) return FFSPMV_ERR_OOM;
+        C.dev_bytes = need;
+    }
+    C.d_mats = (BMat *)C.dev;
+    C.d_items = (BItem *)((char *)C.dev + bm);
+    FF_CUDA(cudaMemcpy(C.d_mats, C.mats_host.data(), sizeof(BMat) * count, cudaMemcpyHostToDevice));
+    if (!W.items.empty())
+        FF_CUDA(cudaMemcpy(C.d_items, W.items.data(), sizeof(BItem) * W.items.size(),
+                           cudaMemcpyHostToDevice));
+    C.nitems = (int)W.items.size();
+    C.chunk_item0 = W.chunk_item0;
+    return FFSPMV_OK;
+}
+
+ffspmv_status launch(const BatchCache &C, int count, const uint32_t *const *d_x,
+                     uint32_t *const *d_y, cudaStream_t st)
+{
+    for (int c = 0; c * kMaxBatch < count; ++c) {
+        const int i0 = C.chunk_item0[c], i1 = C.chunk_item0[c + 1];
+        if (i1 <= i0) continue;
+        BPtrs P;
+        memset(&P, 0, sizeof(P));
+        for (int j = c * kMaxBatch; j < count && j < (c + 1) * kMaxBatch; ++j) {
+            P.x[j - c * kMaxBatch] = d_x[j];
+            P.y[j - c * kMaxBatch] = d_y[j];
+        }
+        k_batch<<<(unsigned)(i1 - i0), kBatchThreads, 0, st>>>(C.d_mats, C.d_items + i0,
+                                                                c * kMaxBatch, P);
+        FF_CUDA(cudaGetLastError());
+    }
+    return FFSPMV_OK;
+}
+
 }  // namespace
 
 // Drop the cached work list if it refers to a handle being destroyed.
@@ -140,85 +278,70 @@ extern "C" ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
     if (count == 0) return FFSPMV_OK;
     cudaStream_t st = (cudaStream_t)stream;
     BatchCache &C = g_cache;
-    bool same = (int)C.hs.size() == count;
-    for (int j = 0; j < count && same; ++j) same = C.hs[j] == hs[j] && C.nvec[j] == nvec[j];
     for (int j = 0; j < count; ++j) {
         if (!hs[j] || nvec[j] < 1 || nvec[j] > 32) return FFSPMV_ERR_ARG;
         if ((hs[j]->A.nrows > 0 && !d_y[j]) || (hs[j]->A.ncols > 0 && !d_x[j])) return FFSPMV_ERR_ARG;
     }
-    if (!same) {
-        C.hs.assign(hs, hs + count);
-        C.nvec.assign(nvec, nvec + count);
-        C.mats_host.assign(count, BMat());
-        std::vector<std::pair<double, BItem>> items;
-        C.chunk_item0.clear();
-        size_t chunk_begin = 0;
-        for (int j = 0; j < count; ++j) {
-            if (j % kMaxBatch == 0) {
-                // order the previous chunk's items by decreasing cost
-                std::stable_sort(items.begin() + chunk_begin, items.end(),
-                                 [](const auto &a, const auto &b) { return a.first > b.first; });
-                chunk_begin = items.size();
-                C.chunk_item0.push_back((int)items.size());
-            }
-            ffspmv_handle *h = hs[j];
-            ffspmv_status r = ensure_csr_copy(h);
-            if (r != FFSPMV_OK) return r;
-            BMat &b = C.mats_host[j];
-            memset(&b, 0, sizeof(b));
-            b.ptr = h->d_rowptr;
-            b.col = h->d_col;
-            b.val = h->d_val;
-            b.nrows = h->A.nrows;
-            b.M = make_mod(h->m, 1, 0);
-            b.nvec = nvec[j];
-            b.G = pow2_ceil(nvec[j]);
-            const int groups = kBatchThreads / b.G;
-            const long long *p = h->h_ptr.data();
-            for (long long r0 = 0; r0 < b.nrows; r0 += groups) {
-                long long r1 = std::min(b.nrows, r0 + groups);
-                BItem it;
-                it.mat = j;
-                it.row0 = r0;
-                it.rows = (int)(r1 - r0);
-                double cost = 0;
-                for (long long i = r0; i < r1; ++i) cost = std::max(cost, (double)(p[i + 1] - p[i]));
-                items.push_back({cost, it});
-            }
+    bool same = (int)C.hs.size() == count;
+    for (int j = 0; j < count && same; ++j) same = C.hs[j] == hs[j] && C.nvec[j] == nvec[j];
+    if (same) return launch(C, count, d_x, d_y, st);
+
+    C.hs.assign(hs, hs + count);
+    C.nvec.assign(nvec, nvec + count);
+    C.mats_host.assign(count, BMat());
+    for (int j = 0; j < count; ++j) {
+        ffspmv_status r = ensure_csr_copy(hs[j]);
+        if (r != FFSPMV_OK) {
+            C.hs.clear();
+            return r;
         }
-        std::stable_sort(items.begin() + chunk_begin, items.end(),
-                         [](const auto &a, const auto &b) { return a.first > b.first; });
-        C.nitems = (int)items.size();
-        C.chunk_item0.push_back(C.nitems);
-        size_t bm = (sizeof(BMat) * count + 255) / 256 * 256;
-        size_t need = bm + sizeof(BItem) * items.size() + 256;
-        if (need > C.dev_bytes) {
-            if (C.dev) cudaFree(C.dev);
-            C.dev = nullptr;
-            C.dev_bytes = 0;
-            if (cudaMalloc(&C.dev, need) != cudaSuccess) return FFSPMV_ERR_OOM;
-            C.dev_bytes = need;
+        BMat &b = C.mats_host[j];
+        memset(&b, 0, sizeof(b));
+        b.ptr = hs[j]->d_rowptr;
+        b.col = hs[j]->d_col;
+        b.val = hs[j]->d_val;
+        b.nrows = hs[j]->A.nrows;
+        b.M = make_mod(hs[j]->m, 1, 0);
+        b.nvec = nvec[j];
+        b.G = pow2_ceil(nvec[j]);
+    }
+    // time every shape on this batch (the outputs are written each time, with
+    // the same values) and keep the fastest
+    cudaEvent_t e0, e1;
+    FF_CUDA(cudaEventCreate(&e0));
+    FF_CUDA(cudaEventCreate(&e1));
+    float best_ms = 0;
+    int best = -1;
+    for (int k = 0; k < kNumShapes; ++k) {
+        WorkList W = make_items(C.hs, C.mats_host, kShapes[k]);
+        ffspmv_status r = upload_items(C, W, count);
+        if (r == FFSPMV_OK) r = launch(C, count, d_x, d_y, st);  // warm-up
+        if (r != FFSPMV_OK) {
+            C.hs.clear();
+            return r;
         }
-        C.d_mats = (BMat *)C.dev;
-        C.d_items = (BItem *)((char *)C.dev + bm);
-        std::vector<BItem> flat(items.size());
-        for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].second;
-        FF_CUDA(cudaMemcpy(C.d_items, flat.data(), sizeof(BItem) * flat.size(), cudaMemcpyHostToDevice));
-    }
-    if (!same) {
-        FF_CUDA(cudaMemcpy(C.d_mats, C.mats_host.data(), sizeof(BMat) * count, cudaMemcpyHostToDevice));
-    }
-    for (int c = 0; c * kMaxBatch < count; ++c) {
-        const int i0 = C.chunk_item0[c], i1 = C.chunk_item0[c + 1];
-        if (i1 <= i0) continue;
-        BPtrs P;
-        memset(&P, 0, sizeof(P));
-        for (int j = c * kMaxBatch; j < count && j < (c + 1) * kMaxBatch; ++j) {
-            P.x[j - c * kMaxBatch] = d_x[j];
-            P.y[j - c * kMaxBatch] = d_y[j];
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2; ++rep) launch(C, count, d_x, d_y, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            C.hs.clear();
+            return FFSPMV_ERR_CUDA;
         }
-        k_batch<<<(unsigned)(i1 - i0), kBatchThreads, 0, st>>>(C.d_mats, C.d_items + i0, c * kMaxBatch, P);
-        FF_CUDA(cudaGetLastError());
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0 || ms < best_ms) {
+            best = k;
+            best_ms = ms;
+        }
     }
-    return FFSPMV_OK;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    C.shape = best;
+    WorkList W = make_items(C.hs, C.mats_host, kShapes[best]);
+    ffspmv_status r = upload_items(C, W, count);
+    if (r != FFSPMV_OK) {
+        C.hs.clear();
+        return r;
+    }
+    return launch(C, count, d_x, d_y, st);
 }

@@ -795,7 +795,8 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
             bnnz[b] += L;
             for (long long k = A.ptr[i]; k < A.ptr[i + 1]; ++k) bpm[b] += A.cls[k] != 0;
         }
-        for (int b = 0; b < kBins; ++b) {
+        // longest rows first: their CTAs start early and the short bins fill in
+        for (int b = kBins - 1; b >= 0; --b) {
             Rows &R = rb[b];
             R.n = (long long)R.ids.size();
             if (!R.n) continue;

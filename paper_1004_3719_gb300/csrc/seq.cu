@@ -28,12 +28,13 @@ namespace ff {
 
 namespace {
 
-constexpr int kSeqThreads = 512;
+constexpr int kSeqThreads = 1024;
 constexpr int kS = 16;                            // block width of the persistent kernel
 constexpr int kCPT = 8;                           // components per thread
 constexpr int kTPR = kS / kCPT;                   // threads per row
-constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 256
+constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 512
 constexpr int kMaxEnt = 16;                       // DIA + ELL_R entries per row
+constexpr int kBatch = 2;                         // entries gathered together per thread
 constexpr int kVsStride = 20;                     // halves per staged row (no bank conflicts)
 constexpr unsigned kDefaultSpins = 1u << 22;      // x <= 64 ns sleeps: well under a second
 
@@ -154,7 +155,7 @@ struct __align__(16) SeqSmem {
 // layout guarantees 16 n < 2^31.
 __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned short *Vin,
                                  unsigned short *Vout, int r0, int r1, bool compute,
-                                 bool project, u64 (&pacc)[2][2][4])
+                                 bool project, u32 (&pacc)[2][2][4])
 {
     const int rip = threadIdx.x / kTPR;
     const int c0 = (threadIdx.x % kTPR) * kCPT;
@@ -172,12 +173,12 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned s
 #pragma unroll
                 for (int k = 0; k < kCPT; ++k) acc[k] = 0;
 #pragma unroll
-                for (int e0 = 0; e0 < kMaxEnt; e0 += 4) {
+                for (int e0 = 0; e0 < kMaxEnt; e0 += kBatch) {
                     if (e0 >= ntot) break;
-                    uint4 q[4];
-                    u32 v[4];
+                    uint4 q[kBatch];
+                    u32 v[kBatch];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kBatch; ++u) {
                         const int e = e0 + u;
                         q[u] = make_uint4(0u, 0u, 0u, 0u);
                         v[u] = 0;
@@ -195,7 +196,7 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned s
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kBatch; ++u) {
                         const u32 qq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -218,6 +219,15 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned s
         *reinterpret_cast<uint2 *>(&vs[rip][c0]) = make_uint2(outq.x, outq.y);
         *reinterpret_cast<uint2 *>(&vs[rip][c0 + 4]) = make_uint2(outq.z, outq.w);
         __syncthreads();
+        // each pass adds below 2^29 per element: reduce every 4 passes
+        if ((pass & 3) == 3) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) pacc[i][j][e] = red64(pacc[i][j][e], a.M);
+        }
         const int q16 = (base >> 4) + w;
         if (q16 * 16 < r1) {
             const uint4 A0 = __ldg(a.XF + ((size_t)q16 * 2 + 0) * 32 + lane);
@@ -236,10 +246,8 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned s
                     mma16816(d0, A0, b0, b1);
                     mma16816(d1, A1, b0, b1);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        pacc[vl][nt][e] += (u64)f32_to_u32(d0[e]);
-                        pacc[vl][nt][e] += (u64)f32_to_u32(d1[e]) << 8;
-                    }
+                    for (int e = 0; e < 4; ++e)
+                        pacc[vl][nt][e] += f32_to_u32(d0[e]) + (f32_to_u32(d1[e]) << 8);
                 }
             }
         }
@@ -248,7 +256,7 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned s
 
 // Add the warps' fragments into sm.acc, then write this CTA's partial
 // projection (reduced) and clear the accumulators.
-__device__ void publish_partial(const SeqArgs &a, SeqSmem &sm, int buf, u64 (&pacc)[2][2][4])
+__device__ void publish_partial(const SeqArgs &a, SeqSmem &sm, int buf, u32 (&pacc)[2][2][4])
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -259,7 +267,7 @@ __device__ void publish_partial(const SeqArgs &a, SeqSmem &sm, int buf, u64 (&pa
         u32 c[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            c[e] = red64(pacc[0][nt][e] + (pacc[1][nt][e] << 8), a.M);  // V limb weights 1, 256
+            c[e] = red64((u64)pacc[0][nt][e] + ((u64)pacc[1][nt][e] << 8), a.M);  // V limb weights 1, 256
             pacc[0][nt][e] = pacc[1][nt][e] = 0;
         }
         sm.red[w][g * kS + b] = c[0];
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
     const int r1 = blockIdx.x + 1 == nb ? (int)a.n : (int)(((a.n * (blockIdx.x + 1) / nb) >> 4) << 4);
     if (a.nsteps <= 0 && !a.Vnext) return;
     const bool skip = a.test_skip && blockIdx.x == 0;
-    u64 pacc[2][2][4];
+    u32 pacc[2][2][4];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j)
             for (int e = 0; e < 4; ++e) pacc[i][j][e] = 0;
