@@ -57,8 +57,9 @@ def parse():
                     help="comma list from formats,sequence,batch ('' for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default="",
-                    help="'ax' or 'atx': only run warm-up + --steps launches of that product "
-                         "(no timing, no extras), for an ncu capture")
+                    help="'ax' or 'atx': only run warm-up + --steps launches of that product; "
+                         "'seq': one block sequence of --steps steps on the 100k Wiedemann "
+                         "matrix (no timing, no extras), for an ncu capture")
     return ap.parse_args()
 
 
@@ -371,6 +372,15 @@ def main():
     torch.cuda.set_device(local)
     import paper_1004_3719_gb300 as ff
     ff.build()
+    if args.profile == "seq":
+        W = gen.wiedemann_matrix(seed=1003)
+        X = torch.from_numpy(gen.uniform_block(1003, W.nrows, 16, 65521).view(np.int32)).cuda()
+        Y = torch.from_numpy(gen.uniform_block(1003, W.nrows, 16, 65521, key=1).view(np.int32)).cuda()
+        Mw = ff.Matrix.from_csr(W, transpose_mode=ff.TRANSPOSE.NONE)
+        Mw.block_sequence(X, Y, args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "seq", "steps": args.steps}))
+        return
     m = args.modulus
     A = gen.powerlaw_matrix(seed=SEED, m=m)
     x_host = gen.uniform_block(SEED + rank, A.ncols, 1, m)
