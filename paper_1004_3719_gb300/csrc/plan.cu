@@ -602,17 +602,28 @@ int bin_of_length(long long L)
 
 long long bin_upper(int b) { return b <= 0 ? 0 : (1LL << (b - 1)); }
 
+// The heuristic table of the binned layout.  Sec. 2.4.5 leaves the chooser's
+// constants to per-architecture tuning; these are the per-bin formats that
+// won most often (weighted by entries) in the exhaustive search over the
+// 2000-matrix training family on GB300: ELL_R for single-entry rows, CSR with
+// 2 to 32 lanes per row (about a quarter to half the bin's longest row) up to
+// 512 entries, one CTA per row up to 8192 entries, rows split across CTAs
+// beyond.
 BinChoice heuristic_bin_choice(int b, double pm_fraction, int use_pm1)
 {
     BinChoice c;
-    long long U = bin_upper(b);
-    if (U <= 8) {
+    const long long U = bin_upper(b);
+    if (U <= 1) {
         c.kind = SEG_ELLR;
         c.group = 1;
-    } else if (U <= 256) {
+    } else if (U <= 512) {
+        // lanes per row for U = 2, 4, ..., 512
+        static const int lanes[] = {2, 4, 4, 8, 8, 16, 16, 32, 32};
+        int k = 0;
+        while ((2LL << k) < U) ++k;
         c.kind = SEG_CSR;
-        c.group = (int)std::min<long long>(32, U / 2);
-    } else if (U <= 2048) {
+        c.group = lanes[k];
+    } else if (U <= 8192) {
         c.kind = SEG_CSRBLK;
         c.group = 32;
     } else {
