@@ -49,6 +49,29 @@ struct BPtrs {
     u32 *y[kMaxBatch];
 };
 
+// acc += sum of val[k] * x[col[k] * nvec + lane] for k = k0, k0 + stride, ...
+// below e, four entries at a time so that four gathers are in flight.
+__device__ __forceinline__ void batch_entries(AccWide &acc, const BMat &A, const u32 *__restrict__ x,
+                                              int lane, long long k0, long long e, long long stride)
+{
+    constexpr int U = 4;
+    for (long long k = k0; k < e; k += U * stride) {
+        long long c[U];
+        u32 a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long kk = k + u * stride;
+            c[u] = kk < e ? (long long)__ldg(A.col + kk) : -1;
+            a[u] = kk < e ? __ldg(A.val + kk) : 0u;
+        }
+        u32 xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u] * A.nvec + lane) : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc.mad(a[u], xv[u]);
+    }
+}
+
 __global__ void __launch_bounds__(kBatchThreads)
 k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0,
         const __grid_constant__ BPtrs P)
@@ -70,11 +93,7 @@ k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0
             AccWide acc;
             acc.zero();
             if (active_lane) {
-                for (long long k = s; k < e; ++k) {
-                    const long long c = __ldg(A.col + k);
-                    const u32 a = __ldg(A.val + k);
-                    acc.mad(a, __ldg(x + c * A.nvec + lane));
-                }
+                batch_entries(acc, A, x, lane, s, e, 1);
                 y[row * A.nvec + lane] = (u32)acc.partial(A.M);
             }
         }
@@ -85,13 +104,7 @@ k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0
     const long long s = __ldg(A.ptr + row), e = __ldg(A.ptr + row + 1);
     AccWide acc;
     acc.zero();
-    if (active_lane) {
-        for (long long k = s + grp; k < e; k += groups) {
-            const long long c = __ldg(A.col + k);
-            const u32 a = __ldg(A.val + k);
-            acc.mad(a, __ldg(x + c * A.nvec + lane));
-        }
-    }
+    if (active_lane) batch_entries(acc, A, x, lane, s + grp, e, groups);
     red[threadIdx.x] = active_lane ? acc.partial(A.M) : 0;  // each below m
     __syncthreads();
     for (int half = groups >> 1; half > 0; half >>= 1) {
