@@ -28,14 +28,15 @@ namespace ff {
 
 namespace {
 
-constexpr int kSeqThreads = 1024;
+constexpr int kSeqThreads = 512;
 constexpr int kS = 16;                            // block width of the persistent kernel
 constexpr int kCPT = 8;                           // components per thread
 constexpr int kTPR = kS / kCPT;                   // threads per row
-constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 512
+constexpr int kRowsPerPass = kSeqThreads / kTPR;  // 256
 constexpr int kMaxEnt = 16;                       // DIA + ELL_R entries per row
-constexpr int kBatch = 2;                         // entries gathered together per thread
+constexpr int kBatch = 10;                        // entries gathered together per thread
 constexpr int kVsStride = 20;                     // halves per staged row (no bank conflicts)
+constexpr size_t kXfSmemMax = 160 * 1024;         // shared memory for resident X fragments
 constexpr unsigned kDefaultSpins = 1u << 22;      // x <= 64 ns sleeps: well under a second
 
 struct SeqArgs {
@@ -57,6 +58,7 @@ struct SeqArgs {
     int *status;               // [0] timeout flag
     unsigned spin_limit;
     int test_skip;
+    int xf_smem;               // X fragments of the CTA's rows held in shared memory
     Mod M;
 };
 
@@ -153,9 +155,9 @@ struct __align__(16) SeqSmem {
 // row (8 components each); warp w then runs k-step w of every 256-row pass
 // with both X limbs against both V limbs (8 MMAs).  Indices are 32-bit: the
 // layout guarantees 16 n < 2^31.
-__device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned short *Vin,
-                                 unsigned short *Vout, int r0, int r1, bool compute,
-                                 bool project, u32 (&pacc)[2][2][4])
+__device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const uint4 *xfs,
+                                 const unsigned short *Vin, unsigned short *Vout, int r0, int r1,
+                                 bool compute, bool project, u32 (&pacc)[2][2][4])
 {
     const int rip = threadIdx.x / kTPR;
     const int c0 = (threadIdx.x % kTPR) * kCPT;
@@ -230,8 +232,15 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const unsigned s
         }
         const int q16 = (base >> 4) + w;
         if (q16 * 16 < r1) {
-            const uint4 A0 = __ldg(a.XF + ((size_t)q16 * 2 + 0) * 32 + lane);
-            const uint4 A1 = __ldg(a.XF + ((size_t)q16 * 2 + 1) * 32 + lane);
+            uint4 A0, A1;
+            if (a.xf_smem) {
+                const uint4 *f = xfs + ((size_t)(q16 - (r0 >> 4)) * 2) * 32 + lane;
+                A0 = f[0];
+                A1 = f[32];
+            } else {
+                A0 = __ldg(a.XF + ((size_t)q16 * 2 + 0) * 32 + lane);
+                A1 = __ldg(a.XF + ((size_t)q16 * 2 + 1) * 32 + lane);
+            }
             const int k0 = w * 16;
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
@@ -305,6 +314,7 @@ __device__ void reduce_step(const SeqArgs &a, int buf, long long step)
 __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_constant__ SeqArgs a)
 {
     __shared__ SeqSmem sm;
+    extern __shared__ uint4 xfs[];  // X fragments of this CTA's 16-row groups (if they fit)
     if (threadIdx.x < kMaxEnt) sm.doff[threadIdx.x] = threadIdx.x < a.ndiag ? a.doff[threadIdx.x] : 0;
     __syncthreads();
     const long long nb = gridDim.x;
@@ -312,6 +322,12 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
     const int r0 = (int)(((a.n * blockIdx.x / nb) >> 4) << 4);
     const int r1 = blockIdx.x + 1 == nb ? (int)a.n : (int)(((a.n * (blockIdx.x + 1) / nb) >> 4) << 4);
     if (a.nsteps <= 0 && !a.Vnext) return;
+    if (a.xf_smem) {
+        // constant across steps: keep the CTA's X fragments resident
+        const int q0 = r0 >> 4, q1 = (r1 + 15) >> 4;
+        for (int t = threadIdx.x; t < (q1 - q0) * 64; t += blockDim.x) xfs[t] = __ldg(a.XF + (size_t)q0 * 64 + t);
+        __syncthreads();
+    }
     const bool skip = a.test_skip && blockIdx.x == 0;
     u32 pacc[2][2][4];
     for (int i = 0; i < 2; ++i)
@@ -319,7 +335,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
             for (int e = 0; e < 4; ++e) pacc[i][j][e] = 0;
     // S_0 = X^T Y
     if (a.nsteps > 0) {
-        spmm_and_project(a, sm, a.V0, a.V0, r0, r1, false, true, pacc);
+        spmm_and_project(a, sm, xfs, a.V0, a.V0, r0, r1, false, true, pacc);
         publish_partial(a, sm, 0, pacc);
         if (!grid_barrier(a, skip)) return;
         reduce_step(a, 0, 0);
@@ -331,7 +347,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         const unsigned short *Vin = (i & 1) ? a.V1 : a.V0;
         unsigned short *Vout = (i & 1) ? a.V0 : a.V1;
         const bool proj = i + 1 < a.nsteps;
-        spmm_and_project(a, sm, Vin, Vout, r0, r1, true, proj, pacc);
+        spmm_and_project(a, sm, xfs, Vin, Vout, r0, r1, true, proj, pacc);
         if (proj) publish_partial(a, sm, (int)((i + 1) & 1), pacc);
         if (!grid_barrier(a, false)) return;
         done = i + 1;
@@ -662,7 +678,8 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sequence, kSeqThreads, 0);
+        cudaFuncSetAttribute(k_sequence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXfSmemMax);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sequence, kSeqThreads, kXfSmemMax);
         nblocks = nsm * std::min(per_sm, 1);
         if (!coop || per_sm < 1) persistent = false;
         // keep at least one pass of rows per CTA
@@ -696,6 +713,10 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
     a.status = h->d_status;
     a.spin_limit = h->opt.barrier_spin_limit ? h->opt.barrier_spin_limit : kDefaultSpins;
     a.test_skip = (h->opt.test_hooks & 1) ? 1 : 0;
+    // X fragments of the largest CTA slice: 1 KB per 16-row group (+ 2 groups of rounding)
+    const size_t xf_bytes = (size_t)((n + nblocks - 1) / nblocks / 16 + 2) * 64 * sizeof(uint4);
+    a.xf_smem = xf_bytes <= kXfSmemMax ? 1 : 0;
+    const size_t dyn_smem = a.xf_smem ? xf_bytes : 0;
     a.M = make_mod(h->m, 1, 0);
 
     // the graph: prepare X/Y, clear barrier + status, run the persistent kernel
@@ -716,6 +737,7 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
             memset(&cfg, 0, sizeof(cfg));
             cfg.gridDim = dim3((unsigned)nblocks);
             cfg.blockDim = dim3(kSeqThreads);
+            cfg.dynamicSmemBytes = dyn_smem;
             cfg.stream = cs;
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeCooperative;
