@@ -262,7 +262,7 @@ def timed_steps(torch, fn, steps, flush, stream):
 def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
     sp = stream.cuda_stream
     out = {}
-    fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED", "LEARNED", "EXHAUSTIVE"]
+    fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED", "PANEL", "LEARNED", "EXHAUSTIVE"]
     sel_of = {"LEARNED": ff.SEL.LEARNED, "EXHAUSTIVE": ff.SEL.EXHAUSTIVE}
     for m in moduli:
         A = gen.powerlaw_matrix(seed=SEED, m=m)

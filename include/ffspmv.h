@@ -53,7 +53,8 @@ enum {
     FFSPMV_FMT_COOS = 4,    /* COO_S: CSR over the non-empty rows only (Sec. 2.4.4) */
     FFSPMV_FMT_DIA = 5,     /* diagonals + offsets; refused past a size guard */
     FFSPMV_FMT_HYBRID = 6,  /* paper heuristic: DIA + ELL_R(w) + CSR/COO/COO_S residue (Sec. 2.4.5) */
-    FFSPMV_FMT_BINNED = 7   /* rows binned by length, one format per bin */
+    FFSPMV_FMT_BINNED = 7,  /* rows binned by length, one format per bin */
+    FFSPMV_FMT_PANEL = 8    /* row blocks x column panels, x staged in shared memory */
 };
 
 /* Format selectors (how FFSPMV_FMT_AUTO / FFSPMV_FMT_BINNED pick). */

@@ -15,7 +15,7 @@ class FFSPMVError(RuntimeError):
 
 
 class FMT:
-    AUTO, CSR, ELLR, COO, COOS, DIA, HYBRID, BINNED = range(8)
+    AUTO, CSR, ELLR, COO, COOS, DIA, HYBRID, BINNED, PANEL = range(9)
 
 
 class SEL:

@@ -169,8 +169,30 @@ struct Phase {
     bool has_atomic = false;           // one vector per launch (carry holds one)
 };
 
+// x-panel layout (FFSPMV_FMT_PANEL): CTA c owns rows [blk_row0[c],
+// blk_row0[c+1]) and walks the column panels of width `pcols` in order,
+// staging x[panel] in shared memory; entry words pack (local row << 16 |
+// local column) and are grouped by (row block, panel), rows ascending.
+constexpr int kPanelThreads = 512;
+constexpr int kPanelRowsMax = 8192;           // rows per block: u64 sums in shared memory
+constexpr int kPanelSmemX = 64 * 1024;       // bytes of one staged x panel (two are in flight)
+constexpr int kPanelLong = 256;              // longer rows go to CTA-per-row CSR segments
+
+struct PanelPart {
+    bool on = false;
+    int nblk = 0, npan = 0, pcols = 0;
+    int xb = 4;      // bytes per staged x entry: 2 when m <= 2^16, else 4
+    int vb = 4;      // bytes per value
+    const u32 *blk_row0 = nullptr;  // [nblk + 1]
+    const u32 *seg = nullptr;       // [nblk * npan + 1]
+    const u32 *ent = nullptr;
+    const void *val = nullptr;
+    void *xh = nullptr;             // contiguous copy of one x column (u16 or u32) for one call
+};
+
 // One matrix plan (A or A^T).
 struct Plan {
+    PanelPart panel;
     long long nrows = 0, ncols = 0, nnz = 0;
     int acc_wide = 0;
     int format = 0;

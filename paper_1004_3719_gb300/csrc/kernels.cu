@@ -6,6 +6,8 @@
 // with NV vectors per launch) in integer accumulators and reduces once per
 // output (Sec. 2.2, delayed reduction); +-1 entries flagged in the column
 // word add or subtract x instead of multiplying (Sec. 2.4.2).
+#include <type_traits>
+
 #include "ff_internal.cuh"
 
 namespace ff {
@@ -510,6 +512,120 @@ static PlanParams params_of(const Phase &ph, int acc_wide)
     return pp;
 }
 
+// ---------------------------------------------------------------------------
+// x-panel layout: one CTA per row block.  The column panels of a contiguous
+// copy of x stream through two shared-memory buffers with cp.async (panel
+// p + 1 is in flight while panel p is used); for each panel the CTA adds
+// val * x[col] of its entries into exact 64-bit row sums in shared memory
+// (products below 2^32 when m <= 2^16 are added as they are, larger ones
+// reduced mod m first), and finally writes all its rows.  Rows longer than
+// kPanelLong entries have no entries here; CSR segments add them afterwards.
+template <typename XT>
+__global__ void k_x_stage(const u32 *__restrict__ x, long long ldx, long long n, XT *__restrict__ xs)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) xs[t] = (XT)x[t * ldx];
+}
+
+__device__ __forceinline__ void panel_cp16(u32 dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <int XB, int VB>
+__global__ void __launch_bounds__(kPanelThreads, 1)
+k_panel(const PanelPart P, const void *__restrict__ xstage, u32 *__restrict__ y, long long ldy,
+        const Mod M)
+{
+    extern __shared__ __align__(16) unsigned char panel_smem[];
+    typedef typename std::conditional<XB == 2, unsigned short, u32>::type XT;
+    u64 *acc = reinterpret_cast<u64 *>(panel_smem + 2 * kPanelSmemX);
+    const int c = blockIdx.x;
+    const u32 r0 = __ldg(P.blk_row0 + c), r1 = __ldg(P.blk_row0 + c + 1);
+    const int nr = (int)(r1 - r0);
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) acc[r] = 0;
+    const bool small = (u64)(M.m - 1) * (M.m - 1) <= 0xffffffffull;
+    const u32 sbase = (u32)__cvta_generic_to_shared(panel_smem);
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(xstage);
+    constexpr int kChunks = kPanelSmemX / 16;  // 16-byte pieces of one panel
+    auto issue = [&](int p) {
+        const unsigned char *g = src + (size_t)p * kPanelSmemX;
+        const u32 d = sbase + (u32)(p & 1) * kPanelSmemX;
+        for (int i = threadIdx.x; i < kChunks; i += blockDim.x) panel_cp16(d + 16u * i, g + 16 * i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    issue(0);
+    for (int p = 0; p < P.npan; ++p) {
+        if (p + 1 < P.npan) {
+            issue(p + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();  // panel p is in shared memory for every thread
+        const XT *xs = reinterpret_cast<const XT *>(panel_smem + (p & 1) * kPanelSmemX);
+        const u32 kb = __ldg(P.seg + (long long)c * P.npan + p), ke = __ldg(P.seg + (long long)c * P.npan + p + 1);
+        for (u32 k = kb + threadIdx.x; k < ke; k += 4 * blockDim.x) {
+            u32 e[4], v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const u32 kk = k + u * blockDim.x;
+                e[u] = kk < ke ? ld_stream(P.ent + kk) : 0xffffffffu;
+                v[u] = kk < ke ? (VB == 2 ? ld_stream(reinterpret_cast<const unsigned short *>(P.val) + kk)
+                                          : ld_stream(reinterpret_cast<const u32 *>(P.val) + kk))
+                               : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (e[u] == 0xffffffffu) continue;
+                const u64 t = (u64)v[u] * (u32)xs[e[u] & 0xffffu];
+                atomicAdd(acc + (e[u] >> 16), small ? t : (u64)red64(t, M));
+            }
+        }
+        __syncthreads();  // buffer p & 1 is refilled by the next issue
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        u32 *yp = y + (long long)(r0 + r) * ldy;
+        *yp = combine(red64(acc[r], M), yp, false, M);
+    }
+}
+
+static size_t panel_smem_bytes() { return (size_t)2 * kPanelSmemX + (size_t)kPanelRowsMax * sizeof(u64); }
+
+static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *y, long long ldy,
+                               int vcol, const Mod &M, cudaStream_t st)
+{
+    const PanelPart &pp = P.panel;
+    static unsigned long long attr_set = 0;  // per device (at most 64)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !(attr_set >> dev & 1ull)) {
+        const int b = (int)panel_smem_bytes();
+        cudaFuncSetAttribute(k_panel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(k_panel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(k_panel<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(k_panel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (dev < 64) attr_set |= 1ull << dev;
+    }
+    const unsigned sb = (unsigned)((P.ncols + 255) / 256);
+    if (pp.xb == 2)
+        k_x_stage<unsigned short><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned short *)pp.xh);
+    else
+        k_x_stage<u32><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (u32 *)pp.xh);
+    FF_CUDA(cudaGetLastError());
+    const size_t smem = panel_smem_bytes();
+    if (pp.xb == 2 && pp.vb == 2)
+        k_panel<2, 2><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
+    else if (pp.xb == 2)
+        k_panel<2, 4><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
+    else if (pp.vb == 2)
+        k_panel<4, 2><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
+    else
+        k_panel<4, 4><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
+    FF_CUDA(cudaGetLastError());
+    return FFSPMV_OK;
+}
+
 static int next_chunk(int left, bool has_atomic)
 {
     if (has_atomic) return 1;
@@ -519,7 +635,7 @@ static int next_chunk(int left, bool has_atomic)
 long long count_plan_launches(const Plan &P, int nvec)
 {
     if (P.nrows == 0) return 0;
-    long long n = 0;
+    long long n = P.panel.on ? 2LL * nvec : 0;
     for (const Phase &ph : P.phases) {
         if (ph.segs.empty()) continue;
         for (int c0 = 0; c0 < nvec; c0 += next_chunk(nvec - c0, ph.has_atomic))
@@ -533,6 +649,13 @@ ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
                        cudaStream_t st)
 {
     const Mod M1 = make_mod(m, alpha, beta);
+    if (P.panel.on) {
+        // panels first (every row written); the long rows' segments then add in
+        for (int v = 0; v < nvec; ++v) {
+            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st);
+            if (r != FFSPMV_OK) return r;
+        }
+    }
     for (size_t pi = 0; pi < P.phases.size(); ++pi) {
         const Phase &ph = P.phases[pi];
         if (ph.segs.empty()) continue;

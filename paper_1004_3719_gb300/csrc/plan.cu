@@ -66,6 +66,8 @@ struct Mat {
     std::vector<unsigned char> cls;  // 0 general, kPlus, kMinus
 };
 
+long long nnz_of(const Mat &A) { return (long long)A.col.size(); }
+
 unsigned char classify(u32 v, u32 m)
 {
     if (v == 1u) return (unsigned char)kPlus;
@@ -634,6 +636,74 @@ BinChoice heuristic_bin_choice(int b, double pm_fraction, int use_pm1)
     return c;
 }
 
+// x-panel layout: nnz-balanced row blocks of at most kPanelRowsMax rows (about
+// one per SM), column panels that fill kPanelSmemX bytes of staged x.  Rows
+// longer than kPanelLong entries are left out (their entries would pile up on
+// one shared-memory sum); the caller gives them CSR segments that add into y.
+bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_row0, size_t &o_seg,
+                size_t &o_ent, size_t &o_val, size_t &o_xh)
+{
+    const long long n = A.nrows;
+    long long nnz = 0;
+    for (long long i = 0; i < n; ++i) {
+        const long long L = A.ptr[i + 1] - A.ptr[i];
+        if (L <= kPanelLong) nnz += L;
+    }
+    if (n <= 0 || nnz >= (1LL << 32)) return false;
+    const int xb = m <= 65536u ? 2 : 4;
+    const int vb = value_bytes(m);
+    const long long pcols = std::min<long long>(kPanelSmemX / xb, 65536);
+    const long long npan = std::max<long long>(1, (A.ncols + pcols - 1) / pcols);
+    const long long target = std::max<long long>(1, (nnz + 151) / 152);
+    std::vector<u32> row0{0};
+    long long cur = 0;
+    for (long long i = 0; i < n; ++i) {
+        long long L = A.ptr[i + 1] - A.ptr[i];
+        if (L > kPanelLong) L = 0;
+        const long long rows = i - row0.back();
+        if (rows > 0 && (rows >= kPanelRowsMax || cur + L > target)) {
+            row0.push_back((u32)i);
+            cur = 0;
+        }
+        cur += L;
+    }
+    row0.push_back((u32)n);
+    const long long nblk = (long long)row0.size() - 1;
+    std::vector<u32> seg((size_t)(nblk * npan + 1), 0), ent((size_t)nnz);
+    std::vector<unsigned char> val((size_t)nnz * vb);
+    auto is_short = [&](long long i) { return A.ptr[i + 1] - A.ptr[i] <= kPanelLong; };
+    for (long long c = 0; c < nblk; ++c)
+        for (long long i = row0[c]; i < row0[c + 1]; ++i)
+            if (is_short(i))
+                for (long long k = A.ptr[i]; k < A.ptr[i + 1]; ++k) seg[c * npan + A.col[k] / pcols + 1]++;
+    for (size_t t = 1; t < seg.size(); ++t) seg[t] += seg[t - 1];
+    std::vector<u32> pos(seg.begin(), seg.end() - 1);
+    for (long long c = 0; c < nblk; ++c)
+        for (long long i = row0[c]; i < row0[c + 1]; ++i) {
+            if (!is_short(i)) continue;
+            for (long long k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                const long long p = A.col[k] / pcols;
+                const u32 at = pos[c * npan + p]++;
+                ent[at] = ((u32)(i - row0[c]) << 16) | (u32)(A.col[k] - p * pcols);
+                if (vb == 2) ((unsigned short *)val.data())[at] = (unsigned short)A.val[k];
+                else ((u32 *)val.data())[at] = A.val[k];
+            }
+        }
+    pp.on = true;
+    pp.nblk = (int)nblk;
+    pp.npan = (int)npan;
+    pp.pcols = (int)pcols;
+    pp.xb = xb;
+    pp.vb = vb;
+    o_row0 = B.putv(row0);
+    o_seg = B.putv(seg);
+    o_ent = B.putv(ent);
+    o_val = B.putv(val);
+    std::vector<unsigned char> z((size_t)(npan * pcols) * xb + 64, 0);
+    o_xh = B.putv(z);
+    return true;
+}
+
 ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                             const long long *ptr, const int *col, const u32 *val,
                             u32 m, const ffspmv_options &opt, const BinChoice *bins)
@@ -833,6 +903,52 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
             phases[0].push_back(s);
         }
         break;
+    }
+    case FFSPMV_FMT_PANEL: {
+        name = "PANEL";
+        size_t o_row0, o_seg, o_ent, o_val, o_xh;
+        if (nnz_of(A) != 0 && make_panel(B, A, m, P.panel, o_row0, o_seg, o_ent, o_val, o_xh)) {
+            // long rows: CTA-per-row (or split) CSR segments adding into y after the panels
+            Rows mid, huge;
+            for (long long i = 0; i < nrows; ++i) {
+                const long long L = A.ptr[i + 1] - A.ptr[i];
+                if (L > 8192) huge.ids.push_back((u32)i);
+                else if (L > kPanelLong) mid.ids.push_back((u32)i);
+            }
+            mid.n = (long long)mid.ids.size();
+            huge.n = (long long)huge.ids.size();
+            if (huge.n) {
+                SegBuild sh;
+                if (!make_csrsplit(B, A, huge, upm, 1, m, sh)) return FFSPMV_ERR_UNSUPPORTED;
+                phases[0].push_back(sh);
+            }
+            if (mid.n) {
+                SegBuild sm;
+                if (!make_csr(B, A, mid, SEG_CSRBLK, 32, upm, 1, m, sm)) return FFSPMV_ERR_UNSUPPORTED;
+                phases[0].push_back(sm);
+            }
+        } else {
+            // nothing to stage: a plain CSR plan
+            SegBuild s;
+            if (!make_csr(B, A, all_rows(nrows), SEG_CSR, G, upm, 0, m, s)) return FFSPMV_ERR_UNSUPPORTED;
+            phases[0].push_back(s);
+            P.panel = PanelPart();
+            break;
+        }
+        ffspmv_status st = finish(P, B, phases);
+        if (st != FFSPMV_OK) return st;
+        unsigned char *base = (unsigned char *)P.arena;
+        P.panel.blk_row0 = (const u32 *)(base + o_row0);
+        P.panel.seg = (const u32 *)(base + o_seg);
+        P.panel.ent = (const u32 *)(base + o_ent);
+        P.panel.val = base + o_val;
+        P.panel.xh = base + o_xh;
+        describe(P, name);
+        char buf[160];
+        snprintf(buf, sizeof buf, "  row blocks %d, column panels %d of %d columns, x staged as %s\n",
+                 P.panel.nblk, P.panel.npan, P.panel.pcols, P.panel.xb == 2 ? "u16" : "u32");
+        P.summary += buf;
+        return FFSPMV_OK;
     }
     default:
         return FFSPMV_ERR_ARG;

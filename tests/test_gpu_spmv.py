@@ -10,7 +10,7 @@ from helpers import rand_block, to_dev, to_host, with_modulus
 
 pytestmark = pytest.mark.gpu
 
-FORMATS = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED"]
+FORMATS = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED", "PANEL"]
 MODULI = [2, 3, 27, 65521, 2**31 - 1, 4294967291]
 
 
@@ -87,7 +87,7 @@ def test_split_long_rows(lib):
     # rows far longer than one CTA chunk, in every plan that splits them
     lengths = np.array([30_000, 1, 9000, 0, 4097, 4096, 4095, 70_000, 2], dtype=np.int64)
     A = gen.uniform_matrix(3, lengths.size, 100_000, lengths, 2**31 - 1, pm_fraction=0.3)
-    for fmt in ("HYBRID", "BINNED", "COO", "CSR"):
+    for fmt in ("HYBRID", "BINNED", "COO", "CSR", "PANEL"):
         for pm in (0, 1):
             M = make(lib, A, fmt, use_pm1=pm)
             check_apply(lib, M, A, alpha=3, beta=4, seed=pm)
@@ -180,7 +180,7 @@ def test_describe_and_info(lib):
 def test_full_size_powerlaw(lib, m):
     # 1M x 1M Zipf (mean 16, max 10k): the benchmark's matrix, checked whole
     A = gen.powerlaw_matrix(seed=1002, m=m)
-    for fmt in ("HYBRID", "BINNED", "CSR"):
+    for fmt in ("HYBRID", "BINNED", "CSR", "PANEL"):
         M = make(lib, A, fmt)
         check_apply(lib, M, A, seed=21)
         check_apply(lib, M, A, transpose=True, seed=22)
