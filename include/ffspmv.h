@@ -54,7 +54,8 @@ enum {
     FFSPMV_FMT_DIA = 5,     /* diagonals + offsets; refused past a size guard */
     FFSPMV_FMT_HYBRID = 6,  /* paper heuristic: DIA + ELL_R(w) + CSR/COO/COO_S residue (Sec. 2.4.5) */
     FFSPMV_FMT_BINNED = 7,  /* rows binned by length, one format per bin */
-    FFSPMV_FMT_PANEL = 8    /* row blocks x column panels, x staged in shared memory */
+    FFSPMV_FMT_PANEL = 8    /* row groups x column groups (CTA clusters), x streamed through
+                               shared memory in panels (not in the paper) */
 };
 
 /* Format selectors (how FFSPMV_FMT_AUTO / FFSPMV_FMT_BINNED pick). */
@@ -209,6 +210,15 @@ ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec,
 ffspmv_status spmv_get_info(ffspmv_t h, int64_t *nrows, int64_t *ncols,
                             int64_t *nnz, uint32_t *modulus,
                             int64_t *device_bytes);
+
+/*
+ * Synchronises `stream`, then reads and clears h's device status word:
+ * FFSPMV_ERR_TIMEOUT if a bounded device wait of an earlier spmv_apply /
+ * spmv_apply_transpose on h ran out (the PANEL kernel's wait for a stage's
+ * copies; the outputs of that call are then wrong), else FFSPMV_OK.  The
+ * apply calls are asynchronous and do not read the word themselves.
+ */
+ffspmv_status spmv_check_status(ffspmv_t h, ffspmv_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -119,6 +119,12 @@ def spmv_count_launches(h, transpose, nvec):
     return n.value
 
 
+def spmv_check_status(h, stream=None):
+    """Synchronise the stream; raise FFSPMVError (FFSPMV_ERR_TIMEOUT) if a
+    bounded device wait of an earlier apply on h ran out."""
+    check(lib().spmv_check_status(h, stream_ptr(stream)), "spmv_check_status")
+
+
 class Matrix:
     """An n x m sparse matrix over Z/mZ resident on the current CUDA device."""
 
@@ -153,6 +159,9 @@ class Matrix:
 
     def launches(self, transpose=False, nvec=1):
         return spmv_count_launches(self.handle, transpose, nvec)
+
+    def check_status(self, stream=None):
+        spmv_check_status(self.handle, stream)
 
     def _run(self, fn, x, y, out_rows, alpha, beta, stream):
         torch = _torch()
@@ -195,6 +204,6 @@ def to_numpy_u32(t):
 __all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
            "spmv_apply_transpose_noalloc",
            "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
-           "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "stream_ptr",
+           "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "spmv_check_status", "stream_ptr",
            "to_numpy_u32",
            "FFSPMVError", "Options"]

@@ -78,6 +78,8 @@ def _declare(L):
     L.spmv_apply_transpose_noalloc.restype = ctypes.c_int
     L.spmv_count_launches.argtypes = [_P, _I32, _I32, ctypes.POINTER(_I64)]
     L.spmv_count_launches.restype = ctypes.c_int
+    L.spmv_check_status.argtypes = [_P, _P]
+    L.spmv_check_status.restype = ctypes.c_int
     for name, args, res in EXTRA_SIGNATURES:
         if hasattr(L, name):
             fn = getattr(L, name)

@@ -230,7 +230,7 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     if (transpose && h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC)
         return run_scatter_transpose(h, d_x, ldx, d_y, ldy, nvec, alpha % h->m, beta % h->m, st);
     const Plan &P = transpose ? h->AT : h->A;
-    return run_plan(P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st);
+    return run_plan(P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, h->d_status + 2);
 }
 
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx, uint32_t *d_y,
@@ -325,6 +325,21 @@ ffspmv_status spmv_get_info(ffspmv_t h, int64_t *nrows, int64_t *ncols, int64_t 
     if (modulus) *modulus = h->m;
     if (device_bytes)
         *device_bytes = (int64_t)(h->A.arena_bytes + h->AT.arena_bytes);
+    return FFSPMV_OK;
+}
+
+ffspmv_status spmv_check_status(ffspmv_t h, ffspmv_stream_t stream)
+{
+    if (!h || !h->d_status) return FFSPMV_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int word = 0;
+    if (cudaMemcpyAsync(&word, h->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return FFSPMV_ERR_CUDA;
+    if (word) {
+        cudaMemsetAsync(h->d_status + 2, 0, sizeof(int), st);
+        return FFSPMV_ERR_TIMEOUT;
+    }
     return FFSPMV_OK;
 }
 

@@ -169,26 +169,59 @@ struct Phase {
     bool has_atomic = false;           // one vector per launch (carry holds one)
 };
 
-// x-panel layout (FFSPMV_FMT_PANEL): CTA c owns rows [blk_row0[c],
-// blk_row0[c+1]) and walks the column panels of width `pcols` in order,
-// staging x[panel] in shared memory; entry words pack (local row << 16 |
-// local column) and are grouped by (row block, panel), rows ascending.
+// x-panel layout (FFSPMV_FMT_PANEL).  Rows are cut into `ngroup` row groups
+// and columns into `q` column groups, both balanced by entries; CTA
+// g * q + j (rank j of a cluster of q CTAs) sums the entries of row group g
+// that fall in column group j.  It walks the panels (`px` bytes of staged x)
+// of its column group that hold any of its entries, starting at a panel that
+// depends on g so that the CTAs do not all read the same x at once.  A stage
+// is at most `pe` entries of one panel; kPanelStages stages are in flight in
+// shared memory, and kPanelStages x slots hold the panels they use (a panel
+// is copied once, with its first stage).  An entry word
+// packs (row in group << kPanelColBits | column in panel); rows ascend within
+// a stage.  Row sums stay in shared memory (u32 sums of terms reduced mod m
+// when m <= 2^16, u64 otherwise); the q CTAs of a cluster add their partial
+// sums through distributed shared memory.
 constexpr int kPanelThreads = 512;
-constexpr int kPanelRowsMax = 8192;           // rows per block: u64 sums in shared memory
-constexpr int kPanelSmemX = 64 * 1024;       // bytes of one staged x panel (two are in flight)
-constexpr int kPanelLong = 256;              // longer rows go to CTA-per-row CSR segments
+constexpr int kPanelPerThread = 8;            // entries a thread takes per step
+constexpr int kPanelStages = 3;
+constexpr int kPanelBarBytes = 32;            // one mbarrier per stage buffer
+constexpr unsigned kPanelSpin = 1u << 20;     // polls of a stage's mbarrier before giving up
+constexpr int kPanelColBits = 15;             // column in panel: at most 32768 slots
+constexpr int kPanelRing = 256;               // stage descriptors held in shared memory
+constexpr long long kPanelLong = 65536;       // longer rows go to split CSR segments
+constexpr int kPanelSmemMax = 227 * 1024;
+
+struct PanelStage {
+    u32 xoff;  // first staged-x element of the panel (a multiple of 8)
+    u32 k0;    // first entry (a multiple of 8)
+    u32 nent;  // entries, a multiple of 8, at most pe
+    u32 xs;    // x slot (bits 0-1); bit 2 set: the panel is copied in with this stage
+};
 
 struct PanelPart {
     bool on = false;
-    int nblk = 0, npan = 0, pcols = 0;
-    int xb = 4;      // bytes per staged x entry: 2 when m <= 2^16, else 4
-    int vb = 4;      // bytes per value
-    const u32 *blk_row0 = nullptr;  // [nblk + 1]
-    const u32 *seg = nullptr;       // [nblk * npan + 1]
+    bool small = true;   // m <= 2^16: u16 x and values, u32 row sums
+    int q = 1;           // CTAs per cluster (column groups)
+    int ngroup = 0;      // row groups
+    int rows_max = 0;    // most rows in one group
+    int resident = 0;    // clusters of q resident at once
+    int px = 0;          // bytes of x per panel (a multiple of 16)
+    int pe = 0;          // entry capacity of a stage (a multiple of 8)
+    int eb = 0;          // bytes per stage's entry buffer (a multiple of 16)
+    long long nstage = 0;
+    size_t smem = 0;     // dynamic shared memory per CTA
+    const u32 *grp_row0 = nullptr;    // [ngroup + 1]
+    const u32 *stage_ptr = nullptr;   // [ngroup * q + 1]
+    const PanelStage *stage = nullptr;
     const u32 *ent = nullptr;
     const void *val = nullptr;
-    void *xh = nullptr;             // contiguous copy of one x column (u16 or u32) for one call
+    void *xh = nullptr;  // contiguous u16 / u32 copy of one x column, zero padded
 };
+
+// Most clusters of q CTAs of the panel kernel resident at once with `smem`
+// bytes of dynamic shared memory each (0 when the launch cannot fit).
+int panel_max_clusters(bool small, int q, size_t smem);
 
 // One matrix plan (A or A^T).
 struct Plan {
@@ -243,7 +276,7 @@ void free_plan(Plan &P);
 // kernels.cu
 ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
                        long long ldy, int nvec, u32 m, u32 alpha, u32 beta,
-                       cudaStream_t st);
+                       cudaStream_t st, int *status = nullptr);
 ffspmv_status run_scatter_transpose(ffspmv_handle *h, const u32 *x,
                                     long long ldx, u32 *y, long long ldy,
                                     int nvec, u32 alpha, u32 beta,

@@ -513,13 +513,12 @@ static PlanParams params_of(const Phase &ph, int acc_wide)
 }
 
 // ---------------------------------------------------------------------------
-// x-panel layout: one CTA per row block.  The column panels of a contiguous
-// copy of x stream through two shared-memory buffers with cp.async (panel
-// p + 1 is in flight while panel p is used); for each panel the CTA adds
-// val * x[col] of its entries into exact 64-bit row sums in shared memory
-// (products below 2^32 when m <= 2^16 are added as they are, larger ones
-// reduced mod m first), and finally writes all its rows.  Rows longer than
-// kPanelLong entries have no entries here; CSR segments add them afterwards.
+// x-panel layout (the layout is described with PanelPart).  x is first copied
+// into a contiguous u16 / u32 array; the panel kernel then streams stages of
+// entries and values, and the x panels they use, into shared memory with
+// cp.async, kPanelStages stages in flight, and adds each term into its row's
+// shared-memory sum.  The terms
+// of a warp that all fall on one row are summed in registers and added once.
 template <typename XT>
 __global__ void k_x_stage(const u32 *__restrict__ x, long long ldx, long long n, XT *__restrict__ xs)
 {
@@ -532,97 +531,255 @@ __device__ __forceinline__ void panel_cp16(u32 dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
-template <int XB, int VB>
-__global__ void __launch_bounds__(kPanelThreads, 1)
-k_panel(const PanelPart P, const void *__restrict__ xstage, u32 *__restrict__ y, long long ldy,
-        const Mod M)
+__device__ __forceinline__ void cluster_sync_all()
 {
-    extern __shared__ __align__(16) unsigned char panel_smem[];
-    typedef typename std::conditional<XB == 2, unsigned short, u32>::type XT;
-    u64 *acc = reinterpret_cast<u64 *>(panel_smem + 2 * kPanelSmemX);
-    const int c = blockIdx.x;
-    const u32 r0 = __ldg(P.blk_row0 + c), r1 = __ldg(P.blk_row0 + c + 1);
-    const int nr = (int)(r1 - r0);
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) acc[r] = 0;
-    const bool small = (u64)(M.m - 1) * (M.m - 1) <= 0xffffffffull;
-    const u32 sbase = (u32)__cvta_generic_to_shared(panel_smem);
-    const unsigned char *src = reinterpret_cast<const unsigned char *>(xstage);
-    constexpr int kChunks = kPanelSmemX / 16;  // 16-byte pieces of one panel
-    auto issue = [&](int p) {
-        const unsigned char *g = src + (size_t)p * kPanelSmemX;
-        const u32 d = sbase + (u32)(p & 1) * kPanelSmemX;
-        for (int i = threadIdx.x; i < kChunks; i += blockDim.x) panel_cp16(d + 16u * i, g + 16 * i);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    issue(0);
-    for (int p = 0; p < P.npan; ++p) {
-        if (p + 1 < P.npan) {
-            issue(p + 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        __syncthreads();  // panel p is in shared memory for every thread
-        const XT *xs = reinterpret_cast<const XT *>(panel_smem + (p & 1) * kPanelSmemX);
-        const u32 kb = __ldg(P.seg + (long long)c * P.npan + p), ke = __ldg(P.seg + (long long)c * P.npan + p + 1);
-        for (u32 k = kb + threadIdx.x; k < ke; k += 4 * blockDim.x) {
-            u32 e[4], v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const u32 kk = k + u * blockDim.x;
-                e[u] = kk < ke ? ld_stream(P.ent + kk) : 0xffffffffu;
-                v[u] = kk < ke ? (VB == 2 ? ld_stream(reinterpret_cast<const unsigned short *>(P.val) + kk)
-                                          : ld_stream(reinterpret_cast<const u32 *>(P.val) + kk))
-                               : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (e[u] == 0xffffffffu) continue;
-                const u64 t = (u64)v[u] * (u32)xs[e[u] & 0xffffu];
-                atomicAdd(acc + (e[u] >> 16), small ? t : (u64)red64(t, M));
-            }
-        }
-        __syncthreads();  // buffer p & 1 is refilled by the next issue
-    }
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-        u32 *yp = y + (long long)(r0 + r) * ldy;
-        *yp = combine(red64(acc[r], M), yp, false, M);
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_cluster(const T *local, u32 rank)
+{
+    u32 a = (u32)__cvta_generic_to_shared(local), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    if constexpr (sizeof(T) == 4) {
+        u32 v;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(r) : "memory");
+        return v;
+    } else {
+        u64 v;
+        asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(r) : "memory");
+        return v;
     }
 }
 
-static size_t panel_smem_bytes() { return (size_t)2 * kPanelSmemX + (size_t)kPanelRowsMax * sizeof(u64); }
+// t mod m for t < 2^32 with mu = floor(2^32 / m): the quotient estimate
+// floor(t * mu / 2^32) is floor(t/m) or one less (Barrett, 1986).
+__device__ __forceinline__ u32 red32(u32 t, u32 m, u32 mu)
+{
+    u32 r = t - __umulhi(t, mu) * m;
+    return r >= m ? r - m : r;
+}
+
+__device__ __forceinline__ void mbar_init(u32 bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> this CTA's shared memory, completing on mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(u32 dst, const void *src, u32 bytes, u32 bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Wait for the phase of `bar` with parity `parity`; false after kPanelSpin polls.
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
+{
+    for (unsigned i = 0; i < kPanelSpin; ++i) {
+        u32 done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <bool SMALL>
+__global__ void __launch_bounds__(kPanelThreads, 1)
+k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int *status)
+{
+    typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
+    typedef typename std::conditional<SMALL, u32, u64>::type AT;
+    constexpr int VB = SMALL ? 2 : 4;
+    extern __shared__ __align__(16) unsigned char panel_smem[];
+    const int PX = P.px, EB = P.eb;
+    // [x slots][entry buffers][stage descriptor ring][mbarriers][row sums]
+    unsigned char *ebuf = panel_smem + kPanelStages * PX;
+    PanelStage *ring = reinterpret_cast<PanelStage *>(ebuf + kPanelStages * EB);
+    unsigned char *bars = reinterpret_cast<unsigned char *>(ring + kPanelRing);
+    AT *acc = reinterpret_cast<AT *>(bars + kPanelBarBytes);
+    const int q = P.q;
+    const int cta = blockIdx.x, g = cta / q, rank = cta % q;
+    const u32 r0 = __ldg(P.grp_row0 + g), nr = __ldg(P.grp_row0 + g + 1) - r0;
+    const u32 s0 = __ldg(P.stage_ptr + cta), ns = __ldg(P.stage_ptr + cta + 1) - s0;
+    const u32 sbase = (u32)__cvta_generic_to_shared(panel_smem);
+    const u32 bar0 = (u32)__cvta_generic_to_shared(bars);
+    const unsigned char *xh = reinterpret_cast<const unsigned char *>(P.xh);
+    const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
+    const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
+    const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
+    const int t = threadIdx.x;
+
+    for (u32 r = t; r < nr; r += kPanelThreads) acc[r] = 0;
+    // descriptors of stages [a, a + kPanelRing / 2) into their ring slots
+    auto load_ring = [&](u32 a) {
+        if (t < kPanelRing / 2 && a + t < ns) ring[(a + t) % kPanelRing] = P.stage[s0 + a + t];
+    };
+    // one thread: the bulk copies of stage s (its x panel when new, entries, values)
+    auto issue = [&](u32 s) {
+        if (s >= ns) return;
+        const PanelStage st = ring[s % kPanelRing];
+        const u32 bar = bar0 + 8u * (s % kPanelStages);
+        const bool newx = (st.xs & 4u) != 0;
+        mbar_expect_tx(bar, (newx ? (u32)PX : 0u) + st.nent * (4u + VB));
+        if (newx) bulk_g2s(sbase + (st.xs & 3u) * PX, xh + (size_t)st.xoff * sizeof(XT), (u32)PX, bar);
+        const u32 d = sbase + kPanelStages * PX + (s % kPanelStages) * EB;
+        bulk_g2s(d, ev + (size_t)st.k0 * 4, st.nent * 4u, bar);
+        bulk_g2s(d + 4u * P.pe, vv + (size_t)st.k0 * VB, st.nent * (u32)VB, bar);
+    };
+    load_ring(0);
+    load_ring(kPanelRing / 2);
+    if (t == 0) {
+        for (int b = 0; b < kPanelStages; ++b) mbar_init(bar0 + 8u * b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0)
+        for (u32 s = 0; s < kPanelStages; ++s) issue(s);
+    bool timed_out = false;
+    for (u32 s = 0; s < ns; ++s) {
+        const PanelStage st = ring[s % kPanelRing];
+        if (mbar_wait(bar0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u)) {
+            const unsigned char *sb = ebuf + (s % kPanelStages) * EB;
+            const XT *xs = reinterpret_cast<const XT *>(panel_smem + (st.xs & 3u) * PX);
+            for (u32 ib = kPanelPerThread * t; ib < st.nent; ib += kPanelPerThread * kPanelThreads) {
+                u32 e[8], v[8];
+                const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * ib);
+                const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * ib + 16);
+                e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
+                e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
+                if (SMALL) {
+                    const uint4 w = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 2 * ib);
+                    v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
+                    v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
+                } else {
+                    const uint4 w0 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib);
+                    const uint4 w1 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib + 16);
+                    v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
+                    v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
+                }
+                AT tm[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const u32 xv = xs[e[u] & ((1u << kPanelColBits) - 1)];
+                    if (SMALL) tm[u] = red32(v[u] * xv, M.m, mu32);
+                    else tm[u] = red64((u64)v[u] * xv, M);
+                }
+                // rows ascend: add each run of equal rows once
+                u32 cur = e[0] >> kPanelColBits;
+                AT w = tm[0];
+#pragma unroll
+                for (int u = 1; u < 8; ++u) {
+                    const u32 r = e[u] >> kPanelColBits;
+                    if (r == cur) {
+                        w += tm[u];
+                    } else {
+                        atomicAdd(acc + cur, w);
+                        cur = r;
+                        w = tm[u];
+                    }
+                }
+                atomicAdd(acc + cur, w);
+            }
+        } else {
+            timed_out = true;
+        }
+        __syncthreads();  // stage s is done with: its buffer takes stage s + kPanelStages
+        if ((s + kPanelStages) % (kPanelRing / 2) == 0 && s + kPanelStages >= kPanelRing) {
+            // the ring half that held stages s + kPanelStages - kPanelRing ... is free
+            load_ring(s + kPanelStages);
+            __syncthreads();
+        }
+        if (t == 0) issue(s + kPanelStages);
+    }
+    if (timed_out) {
+        // a copy never landed: report, and give the last copies a bounded
+        // chance to finish before the CTA leaves
+        if (status) atomicOr(status, 1);
+        for (u32 s = ns > kPanelStages ? ns - kPanelStages : 0; s < ns; ++s)
+            mbar_wait(bar0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u);
+    }
+    __syncthreads();
+    if (q > 1) cluster_sync_all();  // every partial sum of the cluster is final
+    const u32 share = (nr + q - 1) / q, rb = rank * share, re = min(nr, rb + share);
+    for (u32 r = rb + t; r < re; r += kPanelThreads) {
+        u64 sum = 0;
+        for (int j = 0; j < q; ++j) sum += (u64)(q > 1 ? ld_cluster(acc + r, (u32)j) : acc[r]);
+        u32 *yp = y + (long long)(r0 + r) * ldy;
+        *yp = combine(red64(sum, M), yp, false, M);
+    }
+    if (q > 1) cluster_sync_all();  // no CTA leaves while its sums are being read
+}
+
+template <bool SMALL>
+static void panel_set_smem(size_t smem)
+{
+    cudaFuncSetAttribute(k_panel<SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int panel_max_clusters(bool small, int q, size_t smem)
+{
+    if (small) panel_set_smem<true>(smem);
+    else panel_set_smem<false>(smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)q, 1, 1);
+    cfg.blockDim = dim3(kPanelThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)q;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = small ? cudaOccupancyMaxActiveClusters(&n, k_panel<true>, &cfg)
+                          : cudaOccupancyMaxActiveClusters(&n, k_panel<false>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
 
 static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *y, long long ldy,
-                               int vcol, const Mod &M, cudaStream_t st)
+                               int vcol, const Mod &M, cudaStream_t st, int *status)
 {
     const PanelPart &pp = P.panel;
-    static unsigned long long attr_set = 0;  // per device (at most 64)
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !(attr_set >> dev & 1ull)) {
-        const int b = (int)panel_smem_bytes();
-        cudaFuncSetAttribute(k_panel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        cudaFuncSetAttribute(k_panel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        cudaFuncSetAttribute(k_panel<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        cudaFuncSetAttribute(k_panel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        if (dev < 64) attr_set |= 1ull << dev;
-    }
     const unsigned sb = (unsigned)((P.ncols + 255) / 256);
-    if (pp.xb == 2)
+    if (pp.small)
         k_x_stage<unsigned short><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned short *)pp.xh);
     else
         k_x_stage<u32><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (u32 *)pp.xh);
     FF_CUDA(cudaGetLastError());
-    const size_t smem = panel_smem_bytes();
-    if (pp.xb == 2 && pp.vb == 2)
-        k_panel<2, 2><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
-    else if (pp.xb == 2)
-        k_panel<2, 4><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
-    else if (pp.vb == 2)
-        k_panel<4, 2><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
-    else
-        k_panel<4, 4><<<pp.nblk, kPanelThreads, smem, st>>>(pp, pp.xh, y + vcol, ldy, M);
-    FF_CUDA(cudaGetLastError());
+    if (pp.small) panel_set_smem<true>(pp.smem);
+    else panel_set_smem<false>(pp.smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(pp.ngroup * pp.q), 1, 1);
+    cfg.blockDim = dim3(kPanelThreads, 1, 1);
+    cfg.dynamicSmemBytes = pp.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)pp.q;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    u32 *yv = y + vcol;
+    if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, yv, ldy, M, status));
+    else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, yv, ldy, M, status));
     return FFSPMV_OK;
 }
 
@@ -646,13 +803,13 @@ long long count_plan_launches(const Plan &P, int nvec)
 
 ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
                        long long ldy, int nvec, u32 m, u32 alpha, u32 beta,
-                       cudaStream_t st)
+                       cudaStream_t st, int *status)
 {
     const Mod M1 = make_mod(m, alpha, beta);
     if (P.panel.on) {
         // panels first (every row written); the long rows' segments then add in
         for (int v = 0; v < nvec; ++v) {
-            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st);
+            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st, status);
             if (r != FFSPMV_OK) return r;
         }
     }

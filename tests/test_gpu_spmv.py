@@ -94,6 +94,19 @@ def test_split_long_rows(lib):
             check_apply(lib, M, A, nvec=3, seed=pm + 2)
 
 
+@pytest.mark.parametrize("m", [65521, 2**31 - 1])
+def test_panel_clusters(lib, m):
+    # enough columns for clusters of 2-4 CTAs splitting the columns; the
+    # transpose has the power-law skew on its columns instead of its rows
+    A = gen.powerlaw_matrix(seed=8, n=150_001, lmax=20_000, m=m, pm_fraction=0.2)
+    M = make(lib, A, "PANEL")
+    assert "clusters of" in M.describe()
+    check_apply(lib, M, A, alpha=7, beta=5, seed=31)
+    check_apply(lib, M, A, transpose=True, seed=32)
+    check_apply(lib, M, A, nvec=2, seed=33)
+    M.check_status()  # no bounded wait ran out
+
+
 def test_rectangular_and_empty_rows(lib):
     A = gen.random_small(3, 517, 1283, 0.01, 65521, pm_fraction=0.4, dup=True)
     for fmt in FORMATS:
