@@ -262,7 +262,7 @@ def timed_steps(torch, fn, steps, flush, stream):
 def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
     sp = stream.cuda_stream
     out = {}
-    fmts = ["CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED", "PANEL", "LEARNED", "EXHAUSTIVE"]
+    fmts = ["AUTO", "CSR", "ELLR", "COO", "COOS", "DIA", "HYBRID", "BINNED", "PANEL", "LEARNED", "EXHAUSTIVE"]
     sel_of = {"LEARNED": ff.SEL.LEARNED, "EXHAUSTIVE": ff.SEL.EXHAUSTIVE}
     for m in moduli:
         A = gen.powerlaw_matrix(seed=SEED, m=m)
@@ -274,8 +274,9 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
                 key = f if pm < 0 else f"{f}{'+pm1' if pm else '-nopm1'}"
                 try:
                     if f in sel_of:
-                        M = ff.Matrix.from_csr(A, selector=sel_of[f], transpose_mode=ff.TRANSPOSE.NONE,
-                                               use_pm1=pm)
+                        # the selector's per-bin choices, in the binned layout
+                        M = ff.Matrix.from_csr(A, selector=sel_of[f], priority_format=ff.FMT.BINNED,
+                                               transpose_mode=ff.TRANSPOSE.NONE, use_pm1=pm)
                     else:
                         M = ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, f),
                                                transpose_mode=ff.TRANSPOSE.NONE, use_pm1=pm)
@@ -462,9 +463,12 @@ def main():
     ax_ms = statistics.mean(t_ax)
     abytes = algorithmic_bytes(A, m)
     achieved = abytes / (ax_ms / 1e3) / 1e9
+    fmt_a = M.describe().split(":")[0].split()[-1]
+    kname = ("k_panel (y=A*x; the interval also holds its k_x_stage launch)" if fmt_a == "PANEL"
+             else "k_plan (y=A*x)")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": traffic_record("spmv_A_65521"),
-            "kernel": "k_plan (y=A*x)", "algorithmic_bytes": abytes,
+            "frac": round(achieved / hbm, 4), "traffic": traffic_record(f"spmv_A_{m}_{fmt_a}"),
+            "kernel": kname, "algorithmic_bytes": abytes,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
             "launch_ms": round(ax_ms, 4)}
     extra = {"plan": M.describe()}

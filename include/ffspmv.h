@@ -43,8 +43,10 @@ typedef enum {
     FFSPMV_ERR_TIMEOUT = 6      /* a bounded device wait expired (grid barrier) */
 } ffspmv_status;
 
-/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO is the binned layout with
- * the bin formats picked by opt.selector. */
+/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO is the x-panel layout
+ * when m <= 2^16, nnz >= 2^21 and nnz >= 3 * ncols (decided separately for A
+ * and A^T), else the binned layout with the bin formats picked by
+ * opt.selector. */
 enum {
     FFSPMV_FMT_AUTO = 0,
     FFSPMV_FMT_CSR = 1,     /* plain CSR, one fixed thread-group width per row */

@@ -53,10 +53,79 @@ void destroy_handle(ffspmv_handle *h)
     delete h;
 }
 
+// FFSPMV_FMT_AUTO takes the x-panel layout where it beat the binned one on
+// every measured shape: residues below 2^16 (u16 x and values, u32 row sums),
+// at least 2^21 entries (enough to fill the stage pipelines of all SMs) and
+// at least 3 entries per column (each column of x streamed through shared
+// memory serves several entries).  Elsewhere AUTO is BINNED.
+bool panel_preferred(long long ncols, long long nnz, u32 m)
+{
+    return m <= 65536u && nnz >= (1LL << 21) && nnz >= 3 * ncols;
+}
+
+// Mean milliseconds of one y = A x with plan P (x = 0, y scratch), after warm-up.
+float time_whole_plan(const Plan &P, u32 m)
+{
+    u32 *x = nullptr, *y = nullptr;
+    float ms = -1.0f;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&x, (size_t)std::max<long long>(P.ncols, 1) * 4) == cudaSuccess &&
+        cudaMalloc(&y, (size_t)std::max<long long>(P.nrows, 1) * 4) == cudaSuccess &&
+        cudaMemset(x, 0, (size_t)std::max<long long>(P.ncols, 1) * 4) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        const int reps = 5;
+        for (int w = 0; w < 2; ++w) run_plan(P, x, 1, y, 1, 1, m, 1, 0, st);
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps; ++k) run_plan(P, x, 1, y, 1, 1, m, 1, 0, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+            ms /= (float)reps;
+        else
+            ms = -1.0f;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+    cudaGetLastError();
+    return ms;
+}
+
 ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
                                   const long long *ptr, const int *col,
                                   const u32 *val, u32 m, const ffspmv_options &o)
 {
+    const bool exhaustive = o.selector == FFSPMV_SEL_EXHAUSTIVE;
+    if (o.priority_format == FFSPMV_FMT_AUTO && !exhaustive && panel_preferred(ncols, ptr[nrows], m)) {
+        ffspmv_options o2 = o;
+        o2.priority_format = FFSPMV_FMT_PANEL;
+        return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, nullptr);
+    }
+    if (o.priority_format == FFSPMV_FMT_AUTO && exhaustive && m <= 65536u && ptr[nrows] > 0) {
+        // the exhaustive selector also times the whole x-panel plan against
+        // the binned plan of its per-bin winners and keeps the faster
+        ffspmv_options ob = o;
+        ob.priority_format = FFSPMV_FMT_BINNED;
+        Plan B, Q;
+        ffspmv_status sb = build_with_selector(B, nrows, ncols, ptr, col, val, m, ob);
+        if (sb != FFSPMV_OK) return sb;
+        ffspmv_options oq = o;
+        oq.priority_format = FFSPMV_FMT_PANEL;
+        if (build_plan_ex(Q, nrows, ncols, ptr, col, val, m, oq, nullptr) == FFSPMV_OK && Q.panel.on) {
+            const float tb = time_whole_plan(B, m), tq = time_whole_plan(Q, m);
+            if (tq > 0.0f && (tb < 0.0f || tq < tb)) {
+                free_plan(B);
+                P = Q;
+                return FFSPMV_OK;
+            }
+        }
+        free_plan(Q);
+        P = B;
+        return FFSPMV_OK;
+    }
     const bool wants_bins = o.priority_format == FFSPMV_FMT_BINNED ||
                             (o.priority_format == FFSPMV_FMT_AUTO &&
                              (o.selector == FFSPMV_SEL_LEARNED || o.selector == FFSPMV_SEL_EXHAUSTIVE));

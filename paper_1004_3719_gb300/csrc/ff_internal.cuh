@@ -177,18 +177,20 @@ struct Phase {
 // depends on g so that the CTAs do not all read the same x at once.  A stage
 // is at most `pe` entries of one panel; kPanelStages stages are in flight in
 // shared memory, and kPanelStages x slots hold the panels they use (a panel
-// is copied once, with its first stage).  An entry word
+// is copied once, with its first stage).  One warp of the CTA issues the bulk
+// copies of each stage once the buffer's previous stage is done with; the
+// other warps wait for the copies and sum.  An entry word
 // packs (row in group << kPanelColBits | column in panel); rows ascend within
 // a stage.  Row sums stay in shared memory (u32 sums of terms reduced mod m
 // when m <= 2^16, u64 otherwise); the q CTAs of a cluster add their partial
 // sums through distributed shared memory.
-constexpr int kPanelThreads = 512;
+constexpr int kPanelConsumers = 512;          // 16 warps sum entries
+constexpr int kPanelThreads = kPanelConsumers + 32;  // + one warp issuing the copies
 constexpr int kPanelPerThread = 8;            // entries a thread takes per step
 constexpr int kPanelStages = 3;
-constexpr int kPanelBarBytes = 32;            // one mbarrier per stage buffer
-constexpr unsigned kPanelSpin = 1u << 20;     // polls of a stage's mbarrier before giving up
+constexpr int kPanelBarBytes = 64;            // full and empty mbarrier of each stage buffer
+constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
 constexpr int kPanelColBits = 15;             // column in panel: at most 32768 slots
-constexpr int kPanelRing = 256;               // stage descriptors held in shared memory
 constexpr long long kPanelLong = 65536;       // longer rows go to split CSR segments
 constexpr int kPanelSmemMax = 227 * 1024;
 

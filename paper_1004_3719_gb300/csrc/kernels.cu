@@ -595,6 +595,11 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(u32 bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+
 template <bool SMALL>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int *status)
@@ -602,115 +607,128 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
     typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
     constexpr int VB = SMALL ? 2 : 4;
+    constexpr int kWarps = kPanelConsumers / 32;
     extern __shared__ __align__(16) unsigned char panel_smem[];
     const int PX = P.px, EB = P.eb;
-    // [x slots][entry buffers][stage descriptor ring][mbarriers][row sums]
+    // [x slots][entry buffers][full mbarriers][empty mbarriers][row sums]
     unsigned char *ebuf = panel_smem + kPanelStages * PX;
-    PanelStage *ring = reinterpret_cast<PanelStage *>(ebuf + kPanelStages * EB);
-    unsigned char *bars = reinterpret_cast<unsigned char *>(ring + kPanelRing);
+    unsigned char *bars = ebuf + kPanelStages * EB;
     AT *acc = reinterpret_cast<AT *>(bars + kPanelBarBytes);
     const int q = P.q;
     const int cta = blockIdx.x, g = cta / q, rank = cta % q;
     const u32 r0 = __ldg(P.grp_row0 + g), nr = __ldg(P.grp_row0 + g + 1) - r0;
     const u32 s0 = __ldg(P.stage_ptr + cta), ns = __ldg(P.stage_ptr + cta + 1) - s0;
     const u32 sbase = (u32)__cvta_generic_to_shared(panel_smem);
-    const u32 bar0 = (u32)__cvta_generic_to_shared(bars);
-    const unsigned char *xh = reinterpret_cast<const unsigned char *>(P.xh);
-    const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
-    const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
-    const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
-    const int t = threadIdx.x;
+    const u32 full0 = (u32)__cvta_generic_to_shared(bars), empty0 = full0 + 8u * kPanelStages;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
     for (u32 r = t; r < nr; r += kPanelThreads) acc[r] = 0;
-    // descriptors of stages [a, a + kPanelRing / 2) into their ring slots
-    auto load_ring = [&](u32 a) {
-        if (t < kPanelRing / 2 && a + t < ns) ring[(a + t) % kPanelRing] = P.stage[s0 + a + t];
-    };
-    // one thread: the bulk copies of stage s (its x panel when new, entries, values)
-    auto issue = [&](u32 s) {
-        if (s >= ns) return;
-        const PanelStage st = ring[s % kPanelRing];
-        const u32 bar = bar0 + 8u * (s % kPanelStages);
-        const bool newx = (st.xs & 4u) != 0;
-        mbar_expect_tx(bar, (newx ? (u32)PX : 0u) + st.nent * (4u + VB));
-        if (newx) bulk_g2s(sbase + (st.xs & 3u) * PX, xh + (size_t)st.xoff * sizeof(XT), (u32)PX, bar);
-        const u32 d = sbase + kPanelStages * PX + (s % kPanelStages) * EB;
-        bulk_g2s(d, ev + (size_t)st.k0 * 4, st.nent * 4u, bar);
-        bulk_g2s(d + 4u * P.pe, vv + (size_t)st.k0 * VB, st.nent * (u32)VB, bar);
-    };
-    load_ring(0);
-    load_ring(kPanelRing / 2);
     if (t == 0) {
-        for (int b = 0; b < kPanelStages; ++b) mbar_init(bar0 + 8u * b, 1);
+        for (int b = 0; b < kPanelStages; ++b) {
+            mbar_init(full0 + 8u * b, 1);
+            mbar_init(empty0 + 8u * b, kWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (t == 0)
-        for (u32 s = 0; s < kPanelStages; ++s) issue(s);
     bool timed_out = false;
-    for (u32 s = 0; s < ns; ++s) {
-        const PanelStage st = ring[s % kPanelRing];
-        if (mbar_wait(bar0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u)) {
-            const unsigned char *sb = ebuf + (s % kPanelStages) * EB;
-            const XT *xs = reinterpret_cast<const XT *>(panel_smem + (st.xs & 3u) * PX);
-            for (u32 ib = kPanelPerThread * t; ib < st.nent; ib += kPanelPerThread * kPanelThreads) {
-                u32 e[8], v[8];
-                const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * ib);
-                const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * ib + 16);
-                e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
-                e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
-                if (SMALL) {
-                    const uint4 w = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 2 * ib);
-                    v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
-                    v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
-                } else {
-                    const uint4 w0 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib);
-                    const uint4 w1 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib + 16);
-                    v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
-                    v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
+    if (warp == kWarps) {
+        // the copying warp: descriptors 32 at a time, one per lane; lane 0
+        // waits for a buffer to be done with and issues its stage's copies
+        const unsigned char *xh = reinterpret_cast<const unsigned char *>(P.xh);
+        const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
+        const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
+        for (u32 base = 0; base < ns; base += 32) {
+            PanelStage mine = {0, 0, 0, 0};
+            if (base + lane < ns) mine = P.stage[s0 + base + lane];
+            const u32 cnt = min(32u, ns - base);
+            for (u32 i = 0; i < cnt; ++i) {
+                const u32 xoff = __shfl_sync(0xffffffffu, mine.xoff, i);
+                const u32 k0 = __shfl_sync(0xffffffffu, mine.k0, i);
+                const u32 nent = __shfl_sync(0xffffffffu, mine.nent, i);
+                const u32 xs = __shfl_sync(0xffffffffu, mine.xs, i);
+                if (lane == 0) {
+                    const u32 s = base + i, b = s % kPanelStages;
+                    // stage s - kPanelStages (same buffer) must be done with
+                    if (s >= kPanelStages && !mbar_wait(empty0 + 8u * b, (s / kPanelStages - 1) & 1u))
+                        timed_out = true;
+                    const u32 bar = full0 + 8u * b;
+                    const bool newx = (xs & 4u) != 0;
+                    mbar_expect_tx(bar, (newx ? (u32)PX : 0u) + nent * (4u + VB));
+                    if (newx) bulk_g2s(sbase + (xs & 3u) * PX, xh + (size_t)xoff * sizeof(XT), (u32)PX, bar);
+                    const u32 d = sbase + kPanelStages * PX + b * EB;
+                    bulk_g2s(d, ev + (size_t)k0 * 4, nent * 4u, bar);
+                    bulk_g2s(d + 4u * P.pe, vv + (size_t)k0 * VB, nent * (u32)VB, bar);
                 }
-                AT tm[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const u32 xv = xs[e[u] & ((1u << kPanelColBits) - 1)];
-                    if (SMALL) tm[u] = red32(v[u] * xv, M.m, mu32);
-                    else tm[u] = red64((u64)v[u] * xv, M);
-                }
-                // rows ascend: add each run of equal rows once
-                u32 cur = e[0] >> kPanelColBits;
-                AT w = tm[0];
-#pragma unroll
-                for (int u = 1; u < 8; ++u) {
-                    const u32 r = e[u] >> kPanelColBits;
-                    if (r == cur) {
-                        w += tm[u];
-                    } else {
-                        atomicAdd(acc + cur, w);
-                        cur = r;
-                        w = tm[u];
-                    }
-                }
-                atomicAdd(acc + cur, w);
             }
-        } else {
-            timed_out = true;
         }
-        __syncthreads();  // stage s is done with: its buffer takes stage s + kPanelStages
-        if ((s + kPanelStages) % (kPanelRing / 2) == 0 && s + kPanelStages >= kPanelRing) {
-            // the ring half that held stages s + kPanelStages - kPanelRing ... is free
-            load_ring(s + kPanelStages);
-            __syncthreads();
+    } else {
+        const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
+        PanelStage nxt = {0, 0, 0, 0};
+        if (ns > 0) nxt = P.stage[s0];
+        for (u32 s = 0; s < ns; ++s) {
+            const PanelStage st = nxt;
+            if (s + 1 < ns) nxt = P.stage[s0 + s + 1];
+            const u32 b = s % kPanelStages;
+            if (mbar_wait(full0 + 8u * b, (s / kPanelStages) & 1u)) {
+                const unsigned char *sb = ebuf + b * EB;
+                const XT *xs = reinterpret_cast<const XT *>(panel_smem + (st.xs & 3u) * PX);
+                for (u32 ib = kPanelPerThread * t; ib < st.nent; ib += kPanelPerThread * kPanelConsumers) {
+                    u32 e[8], v[8];
+                    const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * ib);
+                    const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * ib + 16);
+                    e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
+                    e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
+                    if (SMALL) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 2 * ib);
+                        v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
+                        v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
+                    } else {
+                        const uint4 w0 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib);
+                        const uint4 w1 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib + 16);
+                        v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
+                        v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
+                    }
+                    AT tm[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const u32 xv = xs[e[u] & ((1u << kPanelColBits) - 1)];
+                        if (SMALL) tm[u] = red32(v[u] * xv, M.m, mu32);
+                        else tm[u] = red64((u64)v[u] * xv, M);
+                    }
+                    // rows ascend: add each run of equal rows once
+                    u32 cur = e[0] >> kPanelColBits;
+                    AT w = tm[0];
+#pragma unroll
+                    for (int u = 1; u < 8; ++u) {
+                        const u32 r = e[u] >> kPanelColBits;
+                        if (r == cur) {
+                            w += tm[u];
+                        } else {
+                            atomicAdd(acc + cur, w);
+                            cur = r;
+                            w = tm[u];
+                        }
+                    }
+                    atomicAdd(acc + cur, w);
+                }
+            } else {
+                timed_out = true;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8u * b);
         }
-        if (t == 0) issue(s + kPanelStages);
     }
-    if (timed_out) {
-        // a copy never landed: report, and give the last copies a bounded
-        // chance to finish before the CTA leaves
-        if (status) atomicOr(status, 1);
-        for (u32 s = ns > kPanelStages ? ns - kPanelStages : 0; s < ns; ++s)
-            mbar_wait(bar0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u);
+    if (__syncthreads_or(timed_out)) {
+        // a copy or a buffer never came: report, and give the last copies a
+        // bounded chance to land before the CTA leaves
+        if (t == 0) {
+            if (status) atomicOr(status, 1);
+            for (u32 s = ns > kPanelStages ? ns - kPanelStages : 0; s < ns; ++s)
+                mbar_wait(full0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (q > 1) cluster_sync_all();  // every partial sum of the cluster is final
     const u32 share = (nr + q - 1) / q, rb = rank * share, re = min(nr, rb + share);
     for (u32 r = rb + t; r < re; r += kPanelThreads) {

@@ -681,10 +681,9 @@ bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size
     const bool small = m <= 65536u;
     const int xb = small ? 2 : 4, vb = small ? 2 : 4, ab = small ? 4 : 8;
     const int ebytes = 4 + vb;
-    const int ring = kPanelRing * (int)sizeof(PanelStage);
     const int min_sb = 8192 + 1024 * ebytes;
     const long long rcap = std::min<long long>(1LL << (32 - kPanelColBits),
-                                               (kPanelSmemMax - ring - kPanelBarBytes - kPanelStages * min_sb) / ab);
+                                               (kPanelSmemMax - kPanelBarBytes - kPanelStages * min_sb) / ab);
 
     // cluster size: fewest waves, then most CTAs busy, then larger q
     int q = 0, nclus = 0;
@@ -729,7 +728,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size
     long long W = 8;
     for (int j = 0; j < q; ++j) W = std::max<long long>(W, cb[j + 1] - cb[j]);
     const long long acc_bytes = (rows_max * ab + 15) / 16 * 16;
-    const long long sb = (kPanelSmemMax - ring - kPanelBarBytes - acc_bytes) / kPanelStages / 16 * 16;  // x slot + entries
+    const long long sb = (kPanelSmemMax - kPanelBarBytes - acc_bytes) / kPanelStages / 16 * 16;  // x slot + entries
     const double dens = (double)nnz / ((double)ng * q) / (double)W;  // entries per column of a CTA
     long long pcols = (long long)((double)sb / ((double)xb + 1.15 * ebytes * dens));
     pcols = std::min<long long>({pcols, 1LL << kPanelColBits, (W + 7) / 8 * 8});
@@ -737,7 +736,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size
     const long long pe = std::min<long long>((sb - pcols * xb) / ebytes / 8 * 8, 1LL << 20);
     if (pe < 8) return false;
     const long long eb = pe * ebytes;  // a multiple of 16
-    const size_t smem = (size_t)(kPanelStages * (pcols * xb + eb) + ring + kPanelBarBytes + acc_bytes);
+    const size_t smem = (size_t)(kPanelStages * (pcols * xb + eb) + kPanelBarBytes + acc_bytes);
 
     std::vector<long long> pbase(q + 1, 0);  // global panel ids by group
     for (int j = 0; j < q; ++j) pbase[j + 1] = pbase[j] + std::max<long long>(1, (cb[j + 1] - cb[j] + pcols - 1) / pcols);
