@@ -180,8 +180,8 @@ struct Phase {
 // is copied once, with its first stage).  One warp of the CTA issues the bulk
 // copies of each stage once the buffer's previous stage is done with; the
 // other warps wait for the copies and sum.  An entry word
-// packs (row in group << kPanelColBits | column in panel); rows ascend within
-// a stage.  Row sums stay in shared memory (u32 sums of terms reduced mod m
+// packs (row in group << kPanelColBits | byte offset of its x in the panel);
+// rows ascend within a stage.  Row sums stay in shared memory (u32 sums of terms reduced mod m
 // when m <= 2^16, u64 otherwise); the q CTAs of a cluster add their partial
 // sums through distributed shared memory.
 constexpr int kPanelConsumers = 512;          // 16 warps sum entries
@@ -189,8 +189,9 @@ constexpr int kPanelThreads = kPanelConsumers + 32;  // + one warp issuing the c
 constexpr int kPanelPerThread = 8;            // entries a thread takes per step
 constexpr int kPanelStages = 3;
 constexpr int kPanelBarBytes = 64;            // full and empty mbarrier of each stage buffer
+constexpr int kPanelDescBytes = 64;           // (entries, x slot) of the stage in each buffer
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
-constexpr int kPanelColBits = 15;             // column in panel: at most 32768 slots
+constexpr int kPanelColBits = 16;             // byte offset of the column in its x panel
 constexpr long long kPanelLong = 65536;       // longer rows go to split CSR segments
 constexpr int kPanelSmemMax = 227 * 1024;
 

@@ -520,10 +520,29 @@ static PlanParams params_of(const Phase &ph, int acc_wide)
 // shared-memory sum.  The terms
 // of a warp that all fall on one row are summed in registers and added once.
 template <typename XT>
-__global__ void k_x_stage(const u32 *__restrict__ x, long long ldx, long long n, XT *__restrict__ xs)
+__global__ void __launch_bounds__(256) k_x_stage(const u32 *__restrict__ x, long long ldx, long long n,
+                                                 XT *__restrict__ xs)
 {
+    const long long nth = (long long)gridDim.x * blockDim.x;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) xs[t] = (XT)x[t * ldx];
+    long long done = 0;
+    if (ldx == 1 && ((uintptr_t)x & 15u) == 0) {
+        // contiguous x: 16-byte loads, four elements each
+        const long long n4 = n / 4;
+        for (long long i = t; i < n4; i += nth) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(x) + i);
+            if constexpr (sizeof(XT) == 2) {
+                uint2 o;
+                o.x = (v.x & 0xffffu) | (v.y << 16);
+                o.y = (v.z & 0xffffu) | (v.w << 16);
+                reinterpret_cast<uint2 *>(xs)[i] = o;
+            } else {
+                reinterpret_cast<uint4 *>(xs)[i] = v;
+            }
+        }
+        done = n4 * 4;
+    }
+    for (long long i = done + t; i < n; i += nth) xs[i] = (XT)x[i * ldx];
 }
 
 __device__ __forceinline__ void panel_cp16(u32 dst, const void *src)
@@ -610,10 +629,11 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
     constexpr int kWarps = kPanelConsumers / 32;
     extern __shared__ __align__(16) unsigned char panel_smem[];
     const int PX = P.px, EB = P.eb;
-    // [x slots][entry buffers][full mbarriers][empty mbarriers][row sums]
+    // [x slots][entry buffers][full mbarriers][empty mbarriers][stage descriptors][row sums]
     unsigned char *ebuf = panel_smem + kPanelStages * PX;
     unsigned char *bars = ebuf + kPanelStages * EB;
-    AT *acc = reinterpret_cast<AT *>(bars + kPanelBarBytes);
+    uint2 *desc = reinterpret_cast<uint2 *>(bars + kPanelBarBytes);  // (entries, x slot) per buffer
+    AT *acc = reinterpret_cast<AT *>(bars + kPanelBarBytes + kPanelDescBytes);
     const int q = P.q;
     const int cta = blockIdx.x, g = cta / q, rank = cta % q;
     const u32 r0 = __ldg(P.grp_row0 + g), nr = __ldg(P.grp_row0 + g + 1) - r0;
@@ -654,6 +674,7 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
                         timed_out = true;
                     const u32 bar = full0 + 8u * b;
                     const bool newx = (xs & 4u) != 0;
+                    desc[b] = make_uint2(nent, xs & 3u);  // published by the arrive below
                     mbar_expect_tx(bar, (newx ? (u32)PX : 0u) + nent * (4u + VB));
                     if (newx) bulk_g2s(sbase + (xs & 3u) * PX, xh + (size_t)xoff * sizeof(XT), (u32)PX, bar);
                     const u32 d = sbase + kPanelStages * PX + b * EB;
@@ -664,16 +685,13 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
         }
     } else {
         const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
-        PanelStage nxt = {0, 0, 0, 0};
-        if (ns > 0) nxt = P.stage[s0];
         for (u32 s = 0; s < ns; ++s) {
-            const PanelStage st = nxt;
-            if (s + 1 < ns) nxt = P.stage[s0 + s + 1];
             const u32 b = s % kPanelStages;
             if (mbar_wait(full0 + 8u * b, (s / kPanelStages) & 1u)) {
+                const uint2 st = desc[b];
                 const unsigned char *sb = ebuf + b * EB;
-                const XT *xs = reinterpret_cast<const XT *>(panel_smem + (st.xs & 3u) * PX);
-                for (u32 ib = kPanelPerThread * t; ib < st.nent; ib += kPanelPerThread * kPanelConsumers) {
+                const unsigned char *xs = panel_smem + st.y * PX;
+                for (u32 ib = kPanelPerThread * t; ib < st.x; ib += kPanelPerThread * kPanelConsumers) {
                     u32 e[8], v[8];
                     const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * ib);
                     const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * ib + 16);
@@ -692,25 +710,17 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
                     AT tm[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const u32 xv = xs[e[u] & ((1u << kPanelColBits) - 1)];
-                        if (SMALL) tm[u] = red32(v[u] * xv, M.m, mu32);
-                        else tm[u] = red64((u64)v[u] * xv, M);
+                        const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & ((1u << kPanelColBits) - 1)));
+                        tm[u] = SMALL ? (AT)red32(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
                     }
-                    // rows ascend: add each run of equal rows once
-                    u32 cur = e[0] >> kPanelColBits;
-                    AT w = tm[0];
+                    if ((e[0] >> kPanelColBits) == (e[7] >> kPanelColBits)) {
+                        // rows ascend: all eight on one row (a long row), one addition
+                        atomicAdd(acc + (e[0] >> kPanelColBits),
+                                  ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7])));
+                    } else {
 #pragma unroll
-                    for (int u = 1; u < 8; ++u) {
-                        const u32 r = e[u] >> kPanelColBits;
-                        if (r == cur) {
-                            w += tm[u];
-                        } else {
-                            atomicAdd(acc + cur, w);
-                            cur = r;
-                            w = tm[u];
-                        }
+                        for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> kPanelColBits), tm[u]);
                     }
-                    atomicAdd(acc + cur, w);
                 }
             } else {
                 timed_out = true;
@@ -775,7 +785,11 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
                                int vcol, const Mod &M, cudaStream_t st, int *status)
 {
     const PanelPart &pp = P.panel;
-    const unsigned sb = (unsigned)((P.ncols + 255) / 256);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned sb =
+        (unsigned)std::max<long long>(1, std::min<long long>((P.ncols / 4 + 255) / 256, 8LL * std::max(nsm, 1)));
     if (pp.small)
         k_x_stage<unsigned short><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned short *)pp.xh);
     else

@@ -683,7 +683,8 @@ bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size
     const int ebytes = 4 + vb;
     const int min_sb = 8192 + 1024 * ebytes;
     const long long rcap = std::min<long long>(1LL << (32 - kPanelColBits),
-                                               (kPanelSmemMax - kPanelBarBytes - kPanelStages * min_sb) / ab);
+                                               (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
+                                                kPanelStages * min_sb) / ab);
 
     // cluster size: fewest waves, then most CTAs busy, then larger q
     int q = 0, nclus = 0;
@@ -728,15 +729,16 @@ bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size
     long long W = 8;
     for (int j = 0; j < q; ++j) W = std::max<long long>(W, cb[j + 1] - cb[j]);
     const long long acc_bytes = (rows_max * ab + 15) / 16 * 16;
-    const long long sb = (kPanelSmemMax - kPanelBarBytes - acc_bytes) / kPanelStages / 16 * 16;  // x slot + entries
+    const long long sb =
+        (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes - acc_bytes) / kPanelStages / 16 * 16;  // x slot + entries
     const double dens = (double)nnz / ((double)ng * q) / (double)W;  // entries per column of a CTA
     long long pcols = (long long)((double)sb / ((double)xb + 1.15 * ebytes * dens));
-    pcols = std::min<long long>({pcols, 1LL << kPanelColBits, (W + 7) / 8 * 8});
+    pcols = std::min<long long>({pcols, (1LL << kPanelColBits) / xb, (W + 7) / 8 * 8});
     pcols = std::max<long long>(8, pcols / 8 * 8);
     const long long pe = std::min<long long>((sb - pcols * xb) / ebytes / 8 * 8, 1LL << 20);
     if (pe < 8) return false;
     const long long eb = pe * ebytes;  // a multiple of 16
-    const size_t smem = (size_t)(kPanelStages * (pcols * xb + eb) + kPanelBarBytes + acc_bytes);
+    const size_t smem = (size_t)(kPanelStages * (pcols * xb + eb) + kPanelBarBytes + kPanelDescBytes + acc_bytes);
 
     std::vector<long long> pbase(q + 1, 0);  // global panel ids by group
     for (int j = 0; j < q; ++j) pbase[j + 1] = pbase[j] + std::max<long long>(1, (cb[j + 1] - cb[j] + pcols - 1) / pcols);
@@ -768,7 +770,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size
                     const long long c = A.col[k], pan = cpan[c];
                     const long long xoff = cb[cgrp[c]] + (pan - pbase[cgrp[c]]) * pcols;
                     const long long at = pos[g * npan + pan]++;
-                    bent[at] = ((u32)(i - row0[g]) << kPanelColBits) | (u32)(c - xoff);
+                    bent[at] = ((u32)(i - row0[g]) << kPanelColBits) | (u32)((c - xoff) * xb);
                     bval[at] = A.val[k];
                 }
             }
