@@ -191,6 +191,7 @@ constexpr int kPanelStages = 3;
 constexpr int kPanelBarBytes = 64;            // full and empty mbarrier of each stage buffer
 constexpr int kPanelDescBytes = 64;           // (entries, x slot) of the stage in each buffer
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
+constexpr int kPanelAhead = 4;                // stages of entries pulled into L2 ahead of use
 constexpr int kPanelColBits = 16;             // byte offset of the column in its x panel
 constexpr long long kPanelLong = 65536;       // longer rows go to split CSR segments
 constexpr int kPanelSmemMax = 227 * 1024;

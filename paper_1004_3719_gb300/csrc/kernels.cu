@@ -523,6 +523,8 @@ template <typename XT>
 __global__ void __launch_bounds__(256) k_x_stage(const u32 *__restrict__ x, long long ldx, long long n,
                                                  XT *__restrict__ xs)
 {
+    // the panel kernel may start now; it waits for this grid before reading xs
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const long long nth = (long long)gridDim.x * blockDim.x;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long done = 0;
@@ -599,6 +601,12 @@ __device__ __forceinline__ void bulk_g2s(u32 dst, const void *src, u32 bytes, u3
                  : "memory");
 }
 
+// Start pulling `bytes` at `src` into L2 (no completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, u32 bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Wait for the phase of `bar` with parity `parity`; false after kPanelSpin polls.
 __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
 {
@@ -658,6 +666,27 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
         const unsigned char *xh = reinterpret_cast<const unsigned char *>(P.xh);
         const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
         const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
+        // the CTA's entries are one range, stage after stage; it is pulled into
+        // L2 kPanelAhead stage capacities ahead of the copies into shared memory
+        u32 kpf = 0, kend = 0;
+        const u32 ahead = (u32)kPanelAhead * (u32)P.pe;
+        auto prefetch_to = [&](u32 want) {
+            want = min(want, kend);
+            while (kpf < want) {
+                const u32 n = min(want - kpf, 8192u);  // entries per prefetch
+                bulk_prefetch_l2(ev + (size_t)kpf * 4, n * 4u);
+                bulk_prefetch_l2(vv + (size_t)kpf * VB, n * (u32)VB);
+                kpf += n;
+            }
+        };
+        if (lane == 0 && ns > 0) {
+            const PanelStage first = P.stage[s0], last = P.stage[s0 + ns - 1];
+            kpf = first.k0;
+            kend = last.k0 + last.nent;
+            prefetch_to(first.k0 + ahead);
+            // staged x is written by the launch before this one
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+        }
         for (u32 base = 0; base < ns; base += 32) {
             PanelStage mine = {0, 0, 0, 0};
             if (base + lane < ns) mine = P.stage[s0 + base + lane];
@@ -680,6 +709,7 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
                     const u32 d = sbase + kPanelStages * PX + b * EB;
                     bulk_g2s(d, ev + (size_t)k0 * 4, nent * 4u, bar);
                     bulk_g2s(d + 4u * P.pe, vv + (size_t)k0 * VB, nent * (u32)VB, bar);
+                    prefetch_to(k0 + nent + ahead);
                 }
             }
         }
@@ -802,13 +832,16 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
     cfg.dynamicSmemBytes = pp.smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)pp.q;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    // start while the staging launch runs; its copying warp waits for it
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     u32 *yv = y + vcol;
     if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, yv, ldy, M, status));
     else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, yv, ldy, M, status));
