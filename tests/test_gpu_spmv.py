@@ -30,6 +30,7 @@ def check_apply(ff, M, A, nvec=1, alpha=1, beta=0, seed=0, transpose=False):
     else:
         M.apply(to_dev(x), yd, alpha=alpha, beta=beta)
         want = oracle.csr_spmv(A, x, y=y0, alpha=alpha, beta=beta)
+    M.check_status()  # no bounded device wait ran out
     got = to_host(yd)
     assert got.shape == want.shape
     bad = np.nonzero(got != want)
