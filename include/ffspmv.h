@@ -88,7 +88,10 @@ typedef struct {
     int32_t sequence_mode;     /* block sequence: 0 = persistent kernel when possible, 1 = one launch per kernel per step */
     int32_t test_hooks;        /* testing only, 0 in normal use: bit 0 = one CTA of the persistent
                                   sequence kernel never arrives at its first grid barrier, so the
-                                  bounded wait of every other CTA runs out (FFSPMV_ERR_TIMEOUT) */
+                                  bounded wait of every other CTA runs out (FFSPMV_ERR_TIMEOUT);
+                                  bit 1 = the x-panel kernel never issues the copies of the second
+                                  stage of each CTA, so the waits for it run out (the status word
+                                  read by spmv_check_status) */
 } ffspmv_options;
 
 /* Fill *opt with the defaults. */

@@ -299,7 +299,10 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     if (transpose && h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC)
         return run_scatter_transpose(h, d_x, ldx, d_y, ldy, nvec, alpha % h->m, beta % h->m, st);
     const Plan &P = transpose ? h->AT : h->A;
-    return run_plan(P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, h->d_status + 2);
+    PanelCtl ctl;
+    ctl.status = h->d_status + 2;
+    ctl.skip_stage = (h->opt.test_hooks & 2) ? 1 : -1;
+    return run_plan(P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, &ctl);
 }
 
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx, uint32_t *d_y,

@@ -278,9 +278,15 @@ ffspmv_status build_plan(Plan &P, long long nrows, long long ncols,
 void free_plan(Plan &P);
 
 // kernels.cu
+// Run-time controls of the x-panel kernel's bounded waits.
+struct PanelCtl {
+    int *status = nullptr;  // device word: bit 0 set when a wait ran out
+    int skip_stage = -1;    // testing only: the copies of this stage of every CTA are never issued
+};
+
 ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
                        long long ldy, int nvec, u32 m, u32 alpha, u32 beta,
-                       cudaStream_t st, int *status = nullptr);
+                       cudaStream_t st, const PanelCtl *ctl = nullptr);
 ffspmv_status run_scatter_transpose(ffspmv_handle *h, const u32 *x,
                                     long long ldx, u32 *y, long long ldy,
                                     int nvec, u32 alpha, u32 beta,

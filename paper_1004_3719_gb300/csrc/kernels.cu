@@ -607,10 +607,11 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, u32 bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-// Wait for the phase of `bar` with parity `parity`; false after kPanelSpin polls.
+// Wait for the phase of `bar` with parity `parity`; false after POLLS polls.
+template <unsigned POLLS = kPanelSpin>
 __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
 {
-    for (unsigned i = 0; i < kPanelSpin; ++i) {
+    for (unsigned i = 0; i < POLLS; ++i) {
         u32 done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
@@ -629,7 +630,7 @@ __device__ __forceinline__ void mbar_arrive(u32 bar)
 
 template <bool SMALL>
 __global__ void __launch_bounds__(kPanelThreads, 1)
-k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int *status)
+k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int *status, int skip_stage)
 {
     typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
@@ -699,8 +700,11 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
                 if (lane == 0) {
                     const u32 s = base + i, b = s % kPanelStages;
                     // stage s - kPanelStages (same buffer) must be done with
-                    if (s >= kPanelStages && !mbar_wait(empty0 + 8u * b, (s / kPanelStages - 1) & 1u))
-                        timed_out = true;
+                    if (s >= kPanelStages) {
+                        const u32 eb = empty0 + 8u * b, ep = (s / kPanelStages - 1) & 1u;
+                        if (!(timed_out ? mbar_wait<1>(eb, ep) : mbar_wait(eb, ep))) timed_out = true;
+                    }
+                    if ((int)s == skip_stage) continue;  // testing: this stage is never issued
                     const u32 bar = full0 + 8u * b;
                     const bool newx = (xs & 4u) != 0;
                     desc[b] = make_uint2(nent, xs & 3u);  // published by the arrive below
@@ -717,7 +721,10 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
         const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
         for (u32 s = 0; s < ns; ++s) {
             const u32 b = s % kPanelStages;
-            if (mbar_wait(full0 + 8u * b, (s / kPanelStages) & 1u)) {
+            // after one wait has run out, the others poll once: a CTA whose
+            // copies stopped coming ends in bounded time
+            const u32 fb = full0 + 8u * b, fp = (s / kPanelStages) & 1u;
+            if (timed_out ? mbar_wait<1>(fb, fp) : mbar_wait(fb, fp)) {
                 const uint2 st = desc[b];
                 const unsigned char *sb = ebuf + b * EB;
                 const unsigned char *xs = panel_smem + st.y * PX;
@@ -765,7 +772,7 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
         if (t == 0) {
             if (status) atomicOr(status, 1);
             for (u32 s = ns > kPanelStages ? ns - kPanelStages : 0; s < ns; ++s)
-                mbar_wait(full0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u);
+                if ((int)s != skip_stage) mbar_wait(full0 + 8u * (s % kPanelStages), (s / kPanelStages) & 1u);
         }
         __syncthreads();
     }
@@ -812,7 +819,7 @@ int panel_max_clusters(bool small, int q, size_t smem)
 }
 
 static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *y, long long ldy,
-                               int vcol, const Mod &M, cudaStream_t st, int *status)
+                               int vcol, const Mod &M, cudaStream_t st, const PanelCtl *ctl)
 {
     const PanelPart &pp = P.panel;
     int dev = 0, nsm = 0;
@@ -843,8 +850,10 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
     cfg.attrs = at;
     cfg.numAttrs = 2;
     u32 *yv = y + vcol;
-    if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, yv, ldy, M, status));
-    else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, yv, ldy, M, status));
+    int *status = ctl ? ctl->status : nullptr;
+    const int skip = ctl ? ctl->skip_stage : -1;
+    if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, yv, ldy, M, status, skip));
+    else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, yv, ldy, M, status, skip));
     return FFSPMV_OK;
 }
 
@@ -868,13 +877,13 @@ long long count_plan_launches(const Plan &P, int nvec)
 
 ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
                        long long ldy, int nvec, u32 m, u32 alpha, u32 beta,
-                       cudaStream_t st, int *status)
+                       cudaStream_t st, const PanelCtl *ctl)
 {
     const Mod M1 = make_mod(m, alpha, beta);
     if (P.panel.on) {
         // panels first (every row written); the long rows' segments then add in
         for (int v = 0; v < nvec; ++v) {
-            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st, status);
+            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st, ctl);
             if (r != FFSPMV_OK) return r;
         }
     }

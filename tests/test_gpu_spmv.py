@@ -108,6 +108,23 @@ def test_panel_clusters(lib, m):
     M.check_status()  # no bounded wait ran out
 
 
+def test_panel_timeout_hook_sets_status_and_handle_survives(lib):
+    # the copies of each CTA's second stage are never issued: the bounded
+    # waits for them run out, the kernel ends, and the status word says so
+    A = gen.powerlaw_matrix(seed=8, n=150_001, lmax=20_000, m=65521)
+    M = make(lib, A, "PANEL", test_hooks=2, transpose_mode=lib.TRANSPOSE.NONE)
+    x = rand_block(1, A.ncols, 1, A.modulus)
+    yd = to_dev(np.zeros(A.nrows, dtype=np.uint32))
+    M.apply(to_dev(x), yd)
+    with pytest.raises(lib.FFSPMVError) as e:
+        M.check_status()
+    assert e.value.status == 6
+    M.check_status()  # read and cleared
+    # the device and the library stay usable
+    N = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE)
+    check_apply(lib, N, A, seed=4)
+
+
 def test_rectangular_and_empty_rows(lib):
     A = gen.random_small(3, 517, 1283, 0.01, 65521, pm_fraction=0.4, dup=True)
     for fmt in FORMATS:
