@@ -2,14 +2,17 @@
 //
 // The work list holds items of two kinds:
 //   rows     a tile of consecutive short rows of one matrix; a group of G
-//            lanes (G = the matrix's block width rounded up to a power of two)
-//            handles one row, lane v accumulating component v, so the x loads
-//            of an entry are contiguous across the group and need no
-//            cross-lane reduction;
+//            lanes handles one row, lane l accumulating the V consecutive
+//            components l*V ... l*V+V-1 (V = 4, 2 or 1, the largest dividing
+//            the block width; G = block width / V rounded up to a power of
+//            two), so the x loads of an entry are contiguous across the group
+//            and need no cross-lane reduction;
 //   long row one row with at least `long_at` entries; the whole CTA shares
 //            its entries (256/G entry lanes x G component lanes) and sums the
 //            partials in shared memory.
-// Each matrix brings its own modulus and Barrett constants (Sec. 2.2).  Items
+// Each matrix brings its own modulus and Barrett constants (Sec. 2.2).  When
+// m <= 2^31 four products (each below 2^62) are summed in a 64-bit word before
+// they are carried into the 96-bit accumulator.  Items
 // are ordered by decreasing estimated cost so that the longest start first.
 // The tile height and the long-row threshold are picked by timing: the first
 // call for a new set of handles and block widths tries a few shapes and
@@ -35,7 +38,9 @@ struct BMat {
     long long nrows;
     Mod M;
     int nvec;
-    int G;
+    int G;      // lanes per row
+    int V;      // components per lane
+    int fold4;  // m <= 2^31: four products fit a 64-bit word
 };
 
 struct BItem {
@@ -49,52 +54,99 @@ struct BPtrs {
     u32 *y[kMaxBatch];
 };
 
-// acc += sum of val[k] * x[col[k] * nvec + lane] for k = k0, k0 + stride, ...
-// below e, four entries at a time so that four gathers are in flight.
-__device__ __forceinline__ void batch_entries(AccWide &acc, const BMat &A, const u32 *__restrict__ x,
-                                              int lane, long long k0, long long e, long long stride)
+__device__ __forceinline__ void acc_add64(AccWide &acc, u64 v)
 {
-    constexpr int U = 4;
-    for (long long k = k0; k < e; k += U * stride) {
-        long long c[U];
-        u32 a[U];
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(acc.w0), "+r"(acc.w1), "+r"(acc.w2)
+        : "r"((u32)v), "r"((u32)(v >> 32)));
+}
+
+// p[0 ... V - 1], one vector load when aligned
+template <int V>
+__device__ __forceinline__ void load_x(u32 (&xv)[V], const u32 *__restrict__ p, bool aligned)
+{
+    if (V == 4 && aligned) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
+        xv[0] = w.x; xv[1] = w.y; xv[2 % V] = w.z; xv[3 % V] = w.w;
+    } else if (V == 2 && aligned) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+        xv[0] = w.x; xv[1 % V] = w.y;
+    } else {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long kk = k + u * stride;
-            c[u] = kk < e ? (long long)__ldg(A.col + kk) : -1;
-            a[u] = kk < e ? __ldg(A.val + kk) : 0u;
-        }
-        u32 xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u] * A.nvec + lane) : 0u;
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc.mad(a[u], xv[u]);
+        for (int v = 0; v < V; ++v) xv[v] = __ldg(p + v);
     }
 }
 
-__global__ void __launch_bounds__(kBatchThreads)
-k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0,
-        const __grid_constant__ BPtrs P)
+// acc[v] += sum of val[k] * xb[col[k] * nvec + v] over k = k0, k0 + stride, ...
+// below L (indices relative to the row's first entry; xb = x + this lane's
+// first component): whole blocks of four entries, four gathers in flight,
+// then the remainder.
+template <int V>
+__device__ __forceinline__ void batch_entries(AccWide (&acc)[V], const BMat &A, const u32 *__restrict__ xb,
+                                              bool aligned, const int *__restrict__ colp,
+                                              const u32 *__restrict__ valp, int k0, int L, int stride)
 {
-    __shared__ u64 red[kBatchThreads];
-    const BItem it = items[blockIdx.x];
-    const BMat &A = mats[it.mat];
-    const u32 *__restrict__ x = P.x[it.mat - mat0];
-    u32 *__restrict__ y = P.y[it.mat - mat0];
+    constexpr int U = 4;
+    const u32 nv = (u32)A.nvec;
+    int k = k0;
+    for (; k + (U - 1) * stride < L; k += U * stride) {
+        u32 c[U], a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = (u32)__ldg(colp + k + u * stride);
+            a[u] = __ldg(valp + k + u * stride);
+        }
+        u32 xv[U][V];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_x<V>(xv[u], xb + (size_t)c[u] * nv, aligned);
+        if (A.fold4) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                u64 sum = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) sum += (u64)a[u] * xv[u][v];
+                acc_add64(acc[v], sum);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v].mad(a[u], xv[u][v]);
+        }
+    }
+    for (; k < L; k += stride) {
+        const u32 c = (u32)__ldg(colp + k), a = __ldg(valp + k);
+        u32 xv[V];
+        load_x<V>(xv, xb + (size_t)c * nv, aligned);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v].mad(a, xv[v]);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void batch_item(const BItem &it, const BMat &A, const u32 *__restrict__ x,
+                                           u32 *__restrict__ y, u64 *red)
+{
     const int G = A.G;
     const int lane = threadIdx.x & (G - 1);
     const int grp = threadIdx.x / G;
     const int groups = kBatchThreads / G;
-    const bool active_lane = lane < A.nvec;
+    const int comp = lane * V;
+    const bool active_lane = comp < A.nvec;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(x) | (uintptr_t)(A.nvec * 4)) & (4 * V - 1)) == 0;
     if (it.rows > 0) {
         for (int r = grp; r < it.rows; r += groups) {
             const long long row = it.row0 + r;
             const long long s = __ldg(A.ptr + row), e = __ldg(A.ptr + row + 1);
-            AccWide acc;
-            acc.zero();
+            AccWide acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v].zero();
             if (active_lane) {
-                batch_entries(acc, A, x, lane, s, e, 1);
-                y[row * A.nvec + lane] = (u32)acc.partial(A.M);
+                batch_entries<V>(acc, A, x + comp, aligned, A.col + s, A.val + s, 0, (int)(e - s), 1);
+#pragma unroll
+                for (int v = 0; v < V; ++v) y[row * A.nvec + comp + v] = (u32)acc[v].partial(A.M);
             }
         }
         return;
@@ -102,16 +154,36 @@ k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0
     // one long row shared by the whole CTA
     const long long row = it.row0;
     const long long s = __ldg(A.ptr + row), e = __ldg(A.ptr + row + 1);
-    AccWide acc;
-    acc.zero();
-    if (active_lane) batch_entries(acc, A, x, lane, s + grp, e, groups);
-    red[threadIdx.x] = active_lane ? acc.partial(A.M) : 0;  // each below m
+    AccWide acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v].zero();
+    if (active_lane) batch_entries<V>(acc, A, x + comp, aligned, A.col + s, A.val + s, grp, (int)(e - s), groups);
+#pragma unroll
+    for (int v = 0; v < V; ++v) red[v * kBatchThreads + threadIdx.x] = active_lane ? acc[v].partial(A.M) : 0;  // each below m
     __syncthreads();
     for (int half = groups >> 1; half > 0; half >>= 1) {
-        if (grp < half) red[threadIdx.x] += red[threadIdx.x + half * G];
+        if (grp < half)
+#pragma unroll
+            for (int v = 0; v < V; ++v) red[v * kBatchThreads + threadIdx.x] += red[v * kBatchThreads + threadIdx.x + half * G];
         __syncthreads();
     }
-    if (grp == 0 && active_lane) y[row * A.nvec + lane] = red64(red[threadIdx.x], A.M);
+    if (grp == 0 && active_lane)
+#pragma unroll
+        for (int v = 0; v < V; ++v) y[row * A.nvec + comp + v] = red64(red[v * kBatchThreads + threadIdx.x], A.M);
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0,
+        const __grid_constant__ BPtrs P)
+{
+    __shared__ u64 red[4 * kBatchThreads];
+    const BItem it = items[blockIdx.x];
+    const BMat &A = mats[it.mat];
+    const u32 *__restrict__ x = P.x[it.mat - mat0];
+    u32 *__restrict__ y = P.y[it.mat - mat0];
+    if (A.V == 4) batch_item<4>(it, A, x, y, red);
+    else if (A.V == 2) batch_item<2>(it, A, x, y, red);
+    else batch_item<1>(it, A, x, y, red);
 }
 
 struct Shape {
@@ -315,8 +387,15 @@ extern "C" ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
         b.val = hs[j]->d_val;
         b.nrows = hs[j]->A.nrows;
         b.M = make_mod(hs[j]->m, 1, 0);
+        // entry indices within a row are 32-bit in the kernel
+        if (hs[j]->A.max_row >= (1LL << 31)) {
+            C.hs.clear();
+            return FFSPMV_ERR_UNSUPPORTED;
+        }
         b.nvec = nvec[j];
-        b.G = pow2_ceil(nvec[j]);
+        b.V = nvec[j] % 4 == 0 ? 4 : nvec[j] % 2 == 0 ? 2 : 1;
+        b.G = pow2_ceil(nvec[j] / b.V);
+        b.fold4 = hs[j]->m <= (1u << 31) ? 1 : 0;
     }
     // time every shape on this batch (the outputs are written each time, with
     // the same values) and keep the fastest
