@@ -39,7 +39,8 @@ struct BMat {
     Mod M;
     int nvec;
     int G;      // lanes per row
-    int V;      // components per lane
+    int V;      // components per lane (the last active lane may have fewer: ragged)
+    int ragged; // nvec is not a multiple of V
     int fold4;  // m <= 2^31: four products fit a 64-bit word
 };
 
@@ -63,11 +64,14 @@ __device__ __forceinline__ void acc_add64(AccWide &acc, u64 v)
         : "r"((u32)v), "r"((u32)(v >> 32)));
 }
 
-// p[0 ... V - 1], one vector load when aligned
-template <int V>
-__device__ __forceinline__ void load_x(u32 (&xv)[V], const u32 *__restrict__ p, bool aligned)
+// p[0 ... V - 1] (the first `cnt` of them when RAG), one vector load when aligned
+template <int V, bool RAG>
+__device__ __forceinline__ void load_x(u32 (&xv)[V], const u32 *__restrict__ p, bool aligned, int cnt)
 {
-    if (V == 4 && aligned) {
+    if (RAG) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) xv[v] = v < cnt ? __ldg(p + v) : 0u;
+    } else if (V == 4 && aligned) {
         const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
         xv[0] = w.x; xv[1] = w.y; xv[2 % V] = w.z; xv[3 % V] = w.w;
     } else if (V == 2 && aligned) {
@@ -83,9 +87,9 @@ __device__ __forceinline__ void load_x(u32 (&xv)[V], const u32 *__restrict__ p, 
 // below L (indices relative to the row's first entry; xb = x + this lane's
 // first component): whole blocks of four entries, four gathers in flight,
 // then the remainder.
-template <int V>
+template <int V, bool RAG>
 __device__ __forceinline__ void batch_entries(AccWide (&acc)[V], const BMat &A, const u32 *__restrict__ xb,
-                                              bool aligned, const int *__restrict__ colp,
+                                              bool aligned, int cnt, const int *__restrict__ colp,
                                               const u32 *__restrict__ valp, int k0, int L, int stride)
 {
     constexpr int U = 4;
@@ -100,7 +104,7 @@ __device__ __forceinline__ void batch_entries(AccWide (&acc)[V], const BMat &A, 
         }
         u32 xv[U][V];
 #pragma unroll
-        for (int u = 0; u < U; ++u) load_x<V>(xv[u], xb + (size_t)c[u] * nv, aligned);
+        for (int u = 0; u < U; ++u) load_x<V, RAG>(xv[u], xb + (size_t)c[u] * nv, aligned, cnt);
         if (A.fold4) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -119,13 +123,13 @@ __device__ __forceinline__ void batch_entries(AccWide (&acc)[V], const BMat &A, 
     for (; k < L; k += stride) {
         const u32 c = (u32)__ldg(colp + k), a = __ldg(valp + k);
         u32 xv[V];
-        load_x<V>(xv, xb + (size_t)c * nv, aligned);
+        load_x<V, RAG>(xv, xb + (size_t)c * nv, aligned, cnt);
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v].mad(a, xv[v]);
     }
 }
 
-template <int V>
+template <int V, bool RAG>
 __device__ __forceinline__ void batch_item(const BItem &it, const BMat &A, const u32 *__restrict__ x,
                                            u32 *__restrict__ y, u64 *red)
 {
@@ -134,7 +138,8 @@ __device__ __forceinline__ void batch_item(const BItem &it, const BMat &A, const
     const int grp = threadIdx.x / G;
     const int groups = kBatchThreads / G;
     const int comp = lane * V;
-    const bool active_lane = comp < A.nvec;
+    const int cnt = min(V, A.nvec - comp);  // components of this lane
+    const bool active_lane = cnt > 0;
     const bool aligned = ((reinterpret_cast<uintptr_t>(x) | (uintptr_t)(A.nvec * 4)) & (4 * V - 1)) == 0;
     if (it.rows > 0) {
         for (int r = grp; r < it.rows; r += groups) {
@@ -144,9 +149,10 @@ __device__ __forceinline__ void batch_item(const BItem &it, const BMat &A, const
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v].zero();
             if (active_lane) {
-                batch_entries<V>(acc, A, x + comp, aligned, A.col + s, A.val + s, 0, (int)(e - s), 1);
+                batch_entries<V, RAG>(acc, A, x + comp, aligned, cnt, A.col + s, A.val + s, 0, (int)(e - s), 1);
 #pragma unroll
-                for (int v = 0; v < V; ++v) y[row * A.nvec + comp + v] = (u32)acc[v].partial(A.M);
+                for (int v = 0; v < V; ++v)
+                    if (!RAG || v < cnt) y[row * A.nvec + comp + v] = (u32)acc[v].partial(A.M);
             }
         }
         return;
@@ -157,7 +163,7 @@ __device__ __forceinline__ void batch_item(const BItem &it, const BMat &A, const
     AccWide acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v].zero();
-    if (active_lane) batch_entries<V>(acc, A, x + comp, aligned, A.col + s, A.val + s, grp, (int)(e - s), groups);
+    if (active_lane) batch_entries<V, RAG>(acc, A, x + comp, aligned, cnt, A.col + s, A.val + s, grp, (int)(e - s), groups);
 #pragma unroll
     for (int v = 0; v < V; ++v) red[v * kBatchThreads + threadIdx.x] = active_lane ? acc[v].partial(A.M) : 0;  // each below m
     __syncthreads();
@@ -169,7 +175,8 @@ __device__ __forceinline__ void batch_item(const BItem &it, const BMat &A, const
     }
     if (grp == 0 && active_lane)
 #pragma unroll
-        for (int v = 0; v < V; ++v) y[row * A.nvec + comp + v] = red64(red[v * kBatchThreads + threadIdx.x], A.M);
+        for (int v = 0; v < V; ++v)
+            if (!RAG || v < cnt) y[row * A.nvec + comp + v] = red64(red[v * kBatchThreads + threadIdx.x], A.M);
 }
 
 __global__ void __launch_bounds__(kBatchThreads)
@@ -181,9 +188,10 @@ k_batch(const BMat *__restrict__ mats, const BItem *__restrict__ items, int mat0
     const BMat &A = mats[it.mat];
     const u32 *__restrict__ x = P.x[it.mat - mat0];
     u32 *__restrict__ y = P.y[it.mat - mat0];
-    if (A.V == 4) batch_item<4>(it, A, x, y, red);
-    else if (A.V == 2) batch_item<2>(it, A, x, y, red);
-    else batch_item<1>(it, A, x, y, red);
+    if (A.ragged) batch_item<4, true>(it, A, x, y, red);
+    else if (A.V == 4) batch_item<4, false>(it, A, x, y, red);
+    else if (A.V == 2) batch_item<2, false>(it, A, x, y, red);
+    else batch_item<1, false>(it, A, x, y, red);
 }
 
 struct Shape {
@@ -393,8 +401,11 @@ extern "C" ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
             return FFSPMV_ERR_UNSUPPORTED;
         }
         b.nvec = nvec[j];
-        b.V = nvec[j] % 4 == 0 ? 4 : nvec[j] % 2 == 0 ? 2 : 1;
-        b.G = pow2_ceil(nvec[j] / b.V);
+        // four components per lane; widths 1 and 2 exactly, others not a
+        // multiple of 4 with a shorter last lane
+        b.V = nvec[j] <= 2 ? nvec[j] : 4;
+        b.ragged = nvec[j] > 2 && nvec[j] % 4 != 0;
+        b.G = pow2_ceil((nvec[j] + b.V - 1) / b.V);
         b.fold4 = hs[j]->m <= (1u << 31) ? 1 : 0;
     }
     // time every shape on this batch (the outputs are written each time, with
