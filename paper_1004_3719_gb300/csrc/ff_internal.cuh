@@ -181,9 +181,10 @@ struct Phase {
 // copies of each stage once the buffer's previous stage is done with; the
 // other warps wait for the copies and sum.  An entry word
 // packs (row in group << kPanelColBits | byte offset of its x in the panel);
-// rows ascend within a stage.  Row sums stay in shared memory (u32 sums of terms reduced mod m
-// when m <= 2^16, u64 otherwise); the q CTAs of a cluster add their partial
-// sums through distributed shared memory.
+// rows ascend within a stage.  Row sums stay in shared memory (u32 sums of
+// terms below 2m when m <= 2^16 -- at most kPanelLong of them, so below 2^32 --
+// u64 sums of terms below m otherwise); the q CTAs of a cluster add their
+// partial sums through distributed shared memory.
 constexpr int kPanelConsumers = 512;          // 16 warps sum entries
 constexpr int kPanelThreads = kPanelConsumers + 32;  // + one warp issuing the copies
 constexpr int kPanelPerThread = 8;            // entries a thread takes per step
@@ -193,7 +194,7 @@ constexpr int kPanelDescBytes = 64;           // (entries, x slot) of the stage 
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
 constexpr int kPanelAhead = 4;                // stages of entries pulled into L2 ahead of use
 constexpr int kPanelColBits = 16;             // byte offset of the column in its x panel
-constexpr long long kPanelLong = 65536;       // longer rows go to split CSR segments
+constexpr long long kPanelLong = 32768;       // longer rows go to split CSR segments
 constexpr int kPanelSmemMax = 227 * 1024;
 
 struct PanelStage {

@@ -573,13 +573,11 @@ __device__ __forceinline__ T ld_cluster(const T *local, u32 rank)
     }
 }
 
-// t mod m for t < 2^32 with mu = floor(2^32 / m): the quotient estimate
-// floor(t * mu / 2^32) is floor(t/m) or one less (Barrett, 1986).
-__device__ __forceinline__ u32 red32(u32 t, u32 m, u32 mu)
-{
-    u32 r = t - __umulhi(t, mu) * m;
-    return r >= m ? r - m : r;
-}
+// A value in [0, 2m) congruent to t mod m, for t < 2^32 and mu = floor(2^32 / m):
+// the quotient estimate floor(t * mu / 2^32) is floor(t/m) or one less
+// (Barrett, 1986); the last conditional subtraction is left to the row sum's
+// final reduction.
+__device__ __forceinline__ u32 red32_lazy(u32 t, u32 m, u32 mu) { return t - __umulhi(t, mu) * m; }
 
 __device__ __forceinline__ void mbar_init(u32 bar, u32 count)
 {
@@ -748,7 +746,7 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & ((1u << kPanelColBits) - 1)));
-                        tm[u] = SMALL ? (AT)red32(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
+                        tm[u] = SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
                     }
                     if ((e[0] >> kPanelColBits) == (e[7] >> kPanelColBits)) {
                         // rows ascend: all eight on one row (a long row), one addition

@@ -125,6 +125,24 @@ def test_panel_timeout_hook_sets_status_and_handle_survives(lib):
     check_apply(lib, N, A, seed=4)
 
 
+def test_panel_longest_rows_worst_values(lib):
+    # m <= 2^16: terms are reduced only below 2m, so a row sum of 32 768 terms
+    # is the most a 32-bit shared-memory sum holds; longer rows leave the
+    # panels.  Every value and every x is m - 1 (the largest terms).
+    m = 65521
+    lengths = np.array([32_768, 32_769, 40_000, 5, 0, 1])
+    n, nc = lengths.size, 100_000
+    col = np.concatenate([np.arange(L) * 2 for L in lengths]).astype(np.int32)
+    A = gen.CSR(n, nc, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col,
+                np.full(lengths.sum(), m - 1, dtype=np.uint32), m)
+    M = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE)
+    assert "panels:" in M.describe()
+    x = np.full(nc, m - 1, dtype=np.uint32)
+    y = to_host(M.apply(to_dev(x)))
+    assert list(y) == [int(L) % m for L in lengths]
+    check_apply(lib, M, A, alpha=2, beta=3, seed=6)
+
+
 def test_rectangular_and_empty_rows(lib):
     A = gen.random_small(3, 517, 1283, 0.01, 65521, pm_fraction=0.4, dup=True)
     for fmt in FORMATS:
