@@ -76,32 +76,30 @@ __device__ __forceinline__ int ld_volatile_int(const int *p)
     return v;
 }
 
-// Grid barrier with a bounded wait.  Returns false (and sets status[0]) when
-// the wait ran out or another CTA already gave up.
-__device__ bool grid_barrier(const SeqArgs &a, bool skip)
+// Grid barrier with a bounded wait.  The arrival counter (zeroed before the
+// launch) only grows: barrier number `epoch` is passed once it reaches
+// epoch * gridDim.x.  One thread per CTA adds its arrival with release order
+// (after the CTA's __syncthreads, so it publishes the whole CTA's writes) and
+// polls with acquire loads.  Returns false (and sets status[0]) when the wait
+// ran out or another CTA already gave up.
+__device__ bool grid_barrier(const SeqArgs &a, bool skip, unsigned &epoch)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        ++epoch;
         if (!skip) {
-            const unsigned gen = ld_acquire(a.bar + 1);
-            __threadfence();
-            const unsigned arrived = atomicAdd(a.bar, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(a.bar, 0u);
-                __threadfence();
-                atomicAdd(a.bar + 1, 1u);
-            } else {
-                unsigned it = 0;
-                while (ld_acquire(a.bar + 1) == gen) {
-                    if (++it > a.spin_limit || ((it & 255u) == 0 && ld_volatile_int(a.status) != 0)) {
-                        atomicExch(a.status, 1);
-                        ok = 0;
-                        break;
-                    }
-                    if (it > 64) __nanosleep(64);
+            const unsigned target = epoch * gridDim.x;
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar) : "memory");
+            unsigned it = 0;
+            while ((int)(ld_acquire(a.bar) - target) < 0) {
+                if (++it > a.spin_limit || ((it & 255u) == 0 && ld_volatile_int(a.status) != 0)) {
+                    atomicExch(a.status, 1);
+                    ok = 0;
+                    break;
                 }
+                if (it > 64) __nanosleep(32);
             }
         } else {
             // test hook: never arrive; wait (bounded) for the others to give up
@@ -110,7 +108,6 @@ __device__ bool grid_barrier(const SeqArgs &a, bool skip)
             atomicExch(a.status, 1);
             ok = 0;
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -329,6 +326,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         __syncthreads();
     }
     const bool skip = a.test_skip && blockIdx.x == 0;
+    unsigned epoch = 0;  // grid barriers passed (thread 0)
     u32 pacc[2][2][4];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j)
@@ -337,7 +335,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
     if (a.nsteps > 0) {
         spmm_and_project(a, sm, xfs, a.V0, a.V0, r0, r1, false, true, pacc);
         publish_partial(a, sm, 0, pacc);
-        if (!grid_barrier(a, skip)) return;
+        if (!grid_barrier(a, skip, epoch)) return;
         reduce_step(a, 0, 0);
     }
     long long done = 0;  // SpMMs done: V_done is current
@@ -349,7 +347,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         const bool proj = i + 1 < a.nsteps;
         spmm_and_project(a, sm, xfs, Vin, Vout, r0, r1, true, proj, pacc);
         if (proj) publish_partial(a, sm, (int)((i + 1) & 1), pacc);
-        if (!grid_barrier(a, false)) return;
+        if (!grid_barrier(a, false, epoch)) return;
         done = i + 1;
         if (proj) reduce_step(a, (int)((i + 1) & 1), i + 1);
     }
