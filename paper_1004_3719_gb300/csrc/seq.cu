@@ -292,14 +292,16 @@ __device__ void publish_partial(const SeqArgs &a, SeqSmem &sm, int buf, u32 (&pa
     __syncthreads();  // sm.red aliases the staging rows of the next step
 }
 
-// S_step[o] = sum over CTAs of their partials (mod p); one warp per output.
+// S_step[o] = sum over CTAs of their partials (mod p); one warp per output,
+// output o on warp o / gridDim.x of CTA o % gridDim.x, so that every CTA has
+// at most two.
 __device__ void reduce_step(const SeqArgs &a, int buf, long long step)
 {
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const u32 *src = a.partial + (size_t)buf * nb * (kS * kS);
-    for (int o = blockIdx.x * nw + w; o < kS * kS; o += nb * nw) {
+    for (int o = blockIdx.x + w * nb; o < kS * kS; o += nb * nw) {
         u64 s = 0;
         for (int c = lane; c < nb; c += 32) s += __ldcg(src + (size_t)c * (kS * kS) + o);
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -331,12 +333,16 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j)
             for (int e = 0; e < 4; ++e) pacc[i][j][e] = 0;
+    // The partials of S_j are summed during the next step, after its SpMM and
+    // before its barrier (they sit in buffer j & 1, which is written again only
+    // after that barrier), so no CTA starts a step late.
+    long long pending = -1;  // step whose partials are published but not yet summed
     // S_0 = X^T Y
     if (a.nsteps > 0) {
         spmm_and_project(a, sm, xfs, a.V0, a.V0, r0, r1, false, true, pacc);
         publish_partial(a, sm, 0, pacc);
         if (!grid_barrier(a, skip, epoch)) return;
-        reduce_step(a, 0, 0);
+        pending = 0;
     }
     long long done = 0;  // SpMMs done: V_done is current
     for (long long i = 0; i < a.nsteps; ++i) {
@@ -346,11 +352,14 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         unsigned short *Vout = (i & 1) ? a.V0 : a.V1;
         const bool proj = i + 1 < a.nsteps;
         spmm_and_project(a, sm, xfs, Vin, Vout, r0, r1, true, proj, pacc);
+        if (pending >= 0) reduce_step(a, (int)(pending & 1), pending);
+        pending = -1;
         if (proj) publish_partial(a, sm, (int)((i + 1) & 1), pacc);
         if (!grid_barrier(a, false, epoch)) return;
         done = i + 1;
-        if (proj) reduce_step(a, (int)((i + 1) & 1), i + 1);
+        if (proj) pending = i + 1;
     }
+    if (pending >= 0) reduce_step(a, (int)(pending & 1), pending);
     if (a.Vnext) {
         const unsigned short *Vf = (done & 1) ? a.V1 : a.V0;
         for (long long t = (long long)r0 * a.s + threadIdx.x; t < (long long)r1 * a.s; t += blockDim.x) {
