@@ -59,7 +59,20 @@ struct SeqArgs {
     unsigned spin_limit;
     int test_skip;
     int xf_smem;               // X fragments of the CTA's rows held in shared memory
+    int mat_smem;              // the CTA's rows of the matrix held in shared memory
+    int mrows;                 // rows of one CTA's resident matrix slice (capacity)
+    int mat_off;               // byte offset of that slice in dynamic shared memory
     Mod M;
+};
+
+// A CTA's rows of the DIA + ELL_R layout, resident in shared memory for the
+// whole launch (the matrix is the same at every step): entry-major like the
+// global arrays, row index relative to the CTA's first row.
+struct MatSlice {
+    const unsigned short *dval;  // [ndiag][mrows]
+    const u32 *col;              // [width][mrows]
+    const unsigned short *val;   // [width][mrows]
+    const u32 *rownb;            // [mrows], or null when all rows have `width` entries
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -152,10 +165,11 @@ struct __align__(16) SeqSmem {
 // row (8 components each); warp w then runs k-step w of every 256-row pass
 // with both X limbs against both V limbs (8 MMAs).  Indices are 32-bit: the
 // layout guarantees 16 n < 2^31.
-__device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const uint4 *xfs,
+__device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const uint4 *xfs, const MatSlice &ms,
                                  const unsigned short *Vin, unsigned short *Vout, int r0, int r1,
                                  bool compute, bool project, u32 (&pacc)[2][2][4])
 {
+    const int R = a.mrows;
     const int rip = threadIdx.x / kTPR;
     const int c0 = (threadIdx.x % kTPR) * kCPT;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -167,7 +181,9 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const uint4 *xfs
         uint4 outq = make_uint4(0u, 0u, 0u, 0u);
         if (row < r1) {
             if (compute) {
-                const int ntot = nd + (a.rownb ? (int)__ldg(a.rownb + row) : a.width);
+                const int lr = row - r0;
+                const int ntot =
+                    nd + (a.rownb ? (a.mat_smem ? (int)ms.rownb[lr] : (int)__ldg(a.rownb + row)) : a.width);
                 u64 acc[kCPT];
 #pragma unroll
                 for (int k = 0; k < kCPT; ++k) acc[k] = 0;
@@ -184,13 +200,20 @@ __device__ void spmm_and_project(const SeqArgs &a, SeqSmem &sm, const uint4 *xfs
                         if (e < nd) {
                             const int j = row + sm.doff[e];
                             if ((unsigned)j < (unsigned)n) {
-                                v[u] = __ldg(a.dval + e * ld + row);
+                                v[u] = a.mat_smem ? ms.dval[e * R + lr] : __ldg(a.dval + e * ld + row);
                                 q[u] = __ldcg(reinterpret_cast<const uint4 *>(Vin + j * kS + c0));
                             }
                         } else if (e < ntot) {
-                            const int idx = (e - nd) * ld + row;
-                            const int j = (int)__ldg(a.col + idx);
-                            v[u] = __ldg(a.val + idx);
+                            int j;
+                            if (a.mat_smem) {
+                                const int li = (e - nd) * R + lr;
+                                j = (int)ms.col[li];
+                                v[u] = ms.val[li];
+                            } else {
+                                const int idx = (e - nd) * ld + row;
+                                j = (int)__ldg(a.col + idx);
+                                v[u] = __ldg(a.val + idx);
+                            }
                             q[u] = __ldcg(reinterpret_cast<const uint4 *>(Vin + j * kS + c0));
                         }
                     }
@@ -325,8 +348,35 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         // constant across steps: keep the CTA's X fragments resident
         const int q0 = r0 >> 4, q1 = (r1 + 15) >> 4;
         for (int t = threadIdx.x; t < (q1 - q0) * 64; t += blockDim.x) xfs[t] = __ldg(a.XF + (size_t)q0 * 64 + t);
-        __syncthreads();
     }
+    MatSlice ms = {nullptr, nullptr, nullptr, nullptr};
+    if (a.mat_smem) {
+        // constant across steps too: the CTA's rows of the matrix
+        unsigned char *base = reinterpret_cast<unsigned char *>(xfs) + a.mat_off;
+        const int R = a.mrows, nr = r1 - r0, ld = (int)a.ld;
+        const size_t b_d = ((size_t)a.ndiag * R * 2 + 15) / 16 * 16, b_c = (size_t)a.width * R * 4;
+        const size_t b_v = ((size_t)a.width * R * 2 + 15) / 16 * 16;
+        unsigned short *dv = reinterpret_cast<unsigned short *>(base);
+        u32 *cl = reinterpret_cast<u32 *>(base + b_d);
+        unsigned short *vl = reinterpret_cast<unsigned short *>(base + b_d + b_c);
+        u32 *rb = a.rownb ? reinterpret_cast<u32 *>(base + b_d + b_c + b_v) : nullptr;
+        for (int t = threadIdx.x; t < a.ndiag * nr; t += blockDim.x) {
+            const int e = t / nr, r = t - e * nr;
+            dv[e * R + r] = __ldg(a.dval + (size_t)e * ld + r0 + r);
+        }
+        for (int t = threadIdx.x; t < a.width * nr; t += blockDim.x) {
+            const int e = t / nr, r = t - e * nr;
+            cl[e * R + r] = __ldg(a.col + (size_t)e * ld + r0 + r);
+            vl[e * R + r] = __ldg(a.val + (size_t)e * ld + r0 + r);
+        }
+        if (rb)
+            for (int r = threadIdx.x; r < nr; r += blockDim.x) rb[r] = __ldg(a.rownb + r0 + r);
+        ms.dval = dv;
+        ms.col = cl;
+        ms.val = vl;
+        ms.rownb = rb;
+    }
+    __syncthreads();
     const bool skip = a.test_skip && blockIdx.x == 0;
     unsigned epoch = 0;  // grid barriers passed (thread 0)
     u32 pacc[2][2][4];
@@ -339,7 +389,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
     long long pending = -1;  // step whose partials are published but not yet summed
     // S_0 = X^T Y
     if (a.nsteps > 0) {
-        spmm_and_project(a, sm, xfs, a.V0, a.V0, r0, r1, false, true, pacc);
+        spmm_and_project(a, sm, xfs, ms, a.V0, a.V0, r0, r1, false, true, pacc);
         publish_partial(a, sm, 0, pacc);
         if (!grid_barrier(a, skip, epoch)) return;
         pending = 0;
@@ -351,7 +401,7 @@ __global__ void __launch_bounds__(kSeqThreads, 1) k_sequence(const __grid_consta
         const unsigned short *Vin = (i & 1) ? a.V1 : a.V0;
         unsigned short *Vout = (i & 1) ? a.V0 : a.V1;
         const bool proj = i + 1 < a.nsteps;
-        spmm_and_project(a, sm, xfs, Vin, Vout, r0, r1, true, proj, pacc);
+        spmm_and_project(a, sm, xfs, ms, Vin, Vout, r0, r1, true, proj, pacc);
         if (pending >= 0) reduce_step(a, (int)(pending & 1), pending);
         pending = -1;
         if (proj) publish_partial(a, sm, (int)((i + 1) & 1), pacc);
@@ -723,7 +773,13 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
     // X fragments of the largest CTA slice: 1 KB per 16-row group (+ 2 groups of rounding)
     const size_t xf_bytes = (size_t)((n + nblocks - 1) / nblocks / 16 + 2) * 64 * sizeof(uint4);
     a.xf_smem = xf_bytes <= kXfSmemMax ? 1 : 0;
-    const size_t dyn_smem = a.xf_smem ? xf_bytes : 0;
+    // the CTA's matrix rows as well, when they fit beside the X fragments
+    a.mrows = (int)(((n + nblocks - 1) / nblocks / 16 + 2) * 16);
+    const size_t mat_bytes = ((size_t)q->ndiag * a.mrows * 2 + 15) / 16 * 16 + (size_t)q->width * a.mrows * 4 +
+                             ((size_t)q->width * a.mrows * 2 + 15) / 16 * 16 + (q->rownb ? (size_t)a.mrows * 4 : 0);
+    a.mat_off = a.xf_smem ? (int)xf_bytes : 0;
+    a.mat_smem = (size_t)a.mat_off + mat_bytes <= kXfSmemMax ? 1 : 0;
+    const size_t dyn_smem = (size_t)a.mat_off + (a.mat_smem ? mat_bytes : 0);
     a.M = make_mod(h->m, 1, 0);
 
     // the graph: prepare X/Y, clear barrier + status, run the persistent kernel
