@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--modulus", type=int, default=65521)
     ap.add_argument("--format", default="AUTO")
     ap.add_argument("--extras", default="formats,sequence",
-                    help="comma list from formats,sequence,batch ('' for none)")
+                    help="comma list from formats,sequence,batch,gf2 ('' for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default="",
                     help="'ax' or 'atx': only run warm-up + --steps launches of that product; "
@@ -364,6 +364,29 @@ def extra_batch(torch, ff, stream):
     return res
 
 
+def extra_gf2(torch, ff, flush, stream):
+    """Y = A X over GF(2) on the same power-law pattern (all values odd at
+    m = 2), 64 and 256 vectors packed in 1 and 4 words per row."""
+    sp = stream.cuda_stream
+    A = gen.powerlaw_matrix(seed=SEED, m=2)
+    M = ff.Matrix.from_csr(A, transpose_mode=ff.TRANSPOSE.NONE)
+    hbm, _ = peaks()
+    res = {"workload": f"powerlaw 1M x 1M pattern ({A.nnz} nnz), GF(2), L2 flushed"}
+    for w in (1, 4):
+        x = torch.from_numpy(gen.uniform_block(SEED, A.ncols, 2 * w, 2**32 - 1).view(np.int64)).cuda()
+        y = torch.empty((A.nrows, w), dtype=torch.int64, device="cuda")
+        fn = lambda: ff.spmv_apply_gf2(M.handle, 0, x, y, w, False, sp)
+        for _ in range(3):
+            fn()
+        ms = statistics.median(timed_steps(torch, fn, 10, flush, stream))
+        # algorithmic bytes: 4 per entry (column), 8 per row pointer, x and y words
+        abytes = 4 * A.nnz + 8 * (A.nrows + 1) + 8 * w * (A.ncols + A.nrows)
+        res[f"words={w}"] = {"ms": round(ms, 4), "gnnz_vec_s": round(A.nnz * 64 * w / ms / 1e6, 1),
+                             "algorithmic_gbs": round(abytes / ms / 1e6, 1),
+                             "hbm_frac": round(abytes / ms / 1e6 / hbm, 3)}
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -485,7 +508,8 @@ def main():
     wanted = [e for e in args.extras.split(",") if e]
     del M
     torch.cuda.empty_cache()
-    for name, fn in (("formats", lambda: extra_formats(torch, ff, flush, stream)),
+    for name, fn in (("gf2", lambda: extra_gf2(torch, ff, flush, stream)),
+                     ("formats", lambda: extra_formats(torch, ff, flush, stream)),
                      ("sequence", lambda: extra_sequence(torch, ff, stream)),
                      ("batch", lambda: extra_batch(torch, ff, stream))):
         if name in wanted:

@@ -217,6 +217,24 @@ ffspmv_status spmv_get_info(ffspmv_t h, int64_t *nrows, int64_t *ncols,
                             int64_t *device_bytes);
 
 /*
+ * Products over GF(2) = Z/2Z with bit-packed vectors (Sec. 2 at m = 2: a sum
+ * is an exclusive or and an entry counts when its value is odd; packing many
+ * vectors into machine words is the binary case the paper's closing remarks
+ * point to): Y = A X (transpose = 0) or Y = A^T X (transpose = 1), or, with
+ * accumulate = 1, Y ^= A X.  h must have modulus 2 (else
+ * FFSPMV_ERR_UNSUPPORTED).  d_X: in_rows x words 64-bit words, row-major,
+ * bit b of word k of row j = component 64k + b of x_j (in_rows = ncols, or
+ * nrows for A^T); d_Y: out_rows x words; words >= 1.  Repeated (i, j) pairs
+ * add up, so an even number of odd copies cancels.  The first call for A (or
+ * A^T) builds the pattern of the odd entries on the device (synchronous);
+ * later calls are stream-ordered and asynchronous.  d_X and d_Y must not
+ * overlap.  Not in the paper as a kernel.
+ */
+ffspmv_status spmv_apply_gf2(ffspmv_t h, int32_t transpose, const uint64_t *d_X,
+                             uint64_t *d_Y, int32_t words, int32_t accumulate,
+                             ffspmv_stream_t stream);
+
+/*
  * Synchronises `stream`, then reads and clears h's device status word:
  * FFSPMV_ERR_TIMEOUT if a bounded device wait of an earlier spmv_apply /
  * spmv_apply_transpose on h ran out (the PANEL kernel's wait for a stage's

@@ -119,6 +119,13 @@ def spmv_count_launches(h, transpose, nvec):
     return n.value
 
 
+def spmv_apply_gf2(h, transpose, x, y, words, accumulate=False, stream=None):
+    """Y = A X (or A^T X; Y ^= ... when accumulate) over GF(2), 64 components
+    per 64-bit word; x, y: device tensors of 64-bit words."""
+    check(lib().spmv_apply_gf2(h, int(transpose), _ptr(x), _ptr(y), int(words), int(bool(accumulate)),
+                               stream_ptr(stream)), "spmv_apply_gf2")
+
+
 def spmv_check_status(h, stream=None):
     """Synchronise the stream; raise FFSPMVError (FFSPMV_ERR_TIMEOUT) if a
     bounded device wait of an earlier apply on h ran out."""
@@ -183,6 +190,22 @@ class Matrix:
         """y <- alpha*A^T*x + beta*y (mod m); x: nrows or nrows x nvec."""
         return self._run(spmv_apply_transpose, x, y, self.ncols, alpha, beta, stream)
 
+    def apply_gf2(self, x, y=None, transpose=False, accumulate=False, stream=None):
+        """Y = A X (or A^T X) over GF(2), or Y ^= ... when accumulate; x: an
+        in_rows x words array of 64-bit words (numpy uint64 or a torch int64
+        tensor), bit b of word k = component 64 k + b."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x).view(np.int64))
+        x = x.to(dev).contiguous()
+        words = x.shape[1] if x.dim() == 2 else 1
+        out_rows = self.ncols if transpose else self.nrows
+        if y is None:
+            y = torch.zeros((out_rows, words) if x.dim() == 2 else (out_rows,), dtype=torch.int64, device=dev)
+        spmv_apply_gf2(self.handle, transpose, x, y, words, accumulate, stream)
+        return y
+
     def block_sequence(self, X, Y, nsteps, want_next=False, stream=None):
         """S_i = X^T A^i Y (mod m), 0 <= i < nsteps; X, Y: n x s."""
         torch = _torch()
@@ -204,6 +227,7 @@ def to_numpy_u32(t):
 __all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
            "spmv_apply_transpose_noalloc",
            "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
-           "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "spmv_check_status", "stream_ptr",
+           "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "spmv_check_status",
+           "spmv_apply_gf2", "stream_ptr",
            "to_numpy_u32",
            "FFSPMVError", "Options"]

@@ -80,6 +80,8 @@ def _declare(L):
     L.spmv_count_launches.restype = ctypes.c_int
     L.spmv_check_status.argtypes = [_P, _P]
     L.spmv_check_status.restype = ctypes.c_int
+    L.spmv_apply_gf2.argtypes = [_P, _I32, _P, _P, _I32, _I32, _P]
+    L.spmv_apply_gf2.restype = ctypes.c_int
     for name, args, res in EXTRA_SIGNATURES:
         if hasattr(L, name):
             fn = getattr(L, name)

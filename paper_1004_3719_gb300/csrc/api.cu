@@ -50,6 +50,7 @@ void destroy_handle(ffspmv_handle *h)
     if (h->d_status) cudaFree(h->d_status);
     free_sequence_state(h);
     batch_forget(h);
+    free_gf2(h);
     delete h;
 }
 

@@ -245,6 +245,10 @@ struct Plan {
 
 }  // namespace ff
 
+namespace ff {
+struct Gf2Pattern;
+}
+
 struct ffspmv_handle {
     ff::Plan A;
     ff::Plan AT;
@@ -268,6 +272,8 @@ struct ffspmv_handle {
     // block sequence state
     void *seq_state = nullptr;
     int *d_status = nullptr;   // device status word (timeouts)
+    // patterns of the odd entries of A and A^T for the GF(2) products
+    ff::Gf2Pattern *gf2[2] = {nullptr, nullptr};
 };
 
 namespace ff {

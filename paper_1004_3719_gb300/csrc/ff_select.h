@@ -14,5 +14,6 @@ ffspmv_status choose_bins(int selector, long long nrows, long long ncols,
 
 void free_sequence_state(ffspmv_handle *h);
 void batch_forget(ffspmv_handle *h);
+void free_gf2(ffspmv_handle *h);
 
 }  // namespace ff
