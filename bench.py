@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--modulus", type=int, default=65521)
     ap.add_argument("--format", default="AUTO")
     ap.add_argument("--extras", default="formats,sequence",
-                    help="comma list from formats,sequence,batch,gf2 ('' for none)")
+                    help="comma list from formats,sequence,batch,gf2,polymat ('' for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default="",
                     help="'ax' or 'atx': only run warm-up + --steps launches of that product; "
@@ -387,6 +387,37 @@ def extra_gf2(torch, ff, flush, stream):
     return res
 
 
+def extra_polymat(torch, ff, stream):
+    """C = A B mod p for 16 x 16 polynomial matrices of degree 6250 each: the
+    top-level product of PM-Basis on the block-Wiedemann sequence of the
+    100k matrix (12 502 terms of 16 x 16)."""
+    import ctypes
+    sp = stream.cuda_stream
+    p, s, d = 65521, 16, 6250
+    A = torch.from_numpy(gen.uniform_block(21, (d + 1) * s, s, p).view(np.int32)).cuda().view(d + 1, s, s)
+    B = torch.from_numpy(gen.uniform_block(22, (d + 1) * s, s, p).view(np.int32)).cuda().view(d + 1, s, s)
+    C = torch.empty((2 * d + 1, s, s), dtype=torch.int32, device="cuda")
+    need = ctypes.c_int64()
+    L = ff.lib()
+    L.polymat_mul_workspace(s, d, d, ctypes.byref(need))
+    work = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    fn = lambda: L.polymat_mul(p, s, d, d, A.data_ptr(), B.data_ptr(), C.data_ptr(), work.data_ptr(),
+                               need.value, sp)
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    schoolbook = s ** 3 * (d + 1) ** 2  # multiply-adds of the plain product
+    return {"workload": f"{s}x{s} polynomial matrices, degree {d} each, p={p}, NTT length 16384 x 3 primes",
+            "ms": round(ms, 3), "schoolbook_equivalent_gmac_s": round(schoolbook / ms / 1e6, 1)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -508,7 +539,8 @@ def main():
     wanted = [e for e in args.extras.split(",") if e]
     del M
     torch.cuda.empty_cache()
-    for name, fn in (("gf2", lambda: extra_gf2(torch, ff, flush, stream)),
+    for name, fn in (("polymat", lambda: extra_polymat(torch, ff, stream)),
+                     ("gf2", lambda: extra_gf2(torch, ff, flush, stream)),
                      ("formats", lambda: extra_formats(torch, ff, flush, stream)),
                      ("sequence", lambda: extra_sequence(torch, ff, stream)),
                      ("batch", lambda: extra_batch(torch, ff, stream))):

@@ -126,6 +126,24 @@ def spmv_apply_gf2(h, transpose, x, y, words, accumulate=False, stream=None):
                                stream_ptr(stream)), "spmv_apply_gf2")
 
 
+def polymat_mul(p, A, B, stream=None):
+    """C = A B mod p for polynomial matrices, coefficient-major (d+1, s, s)
+    arrays of residues (numpy uint32 or torch int32 on the device); returns a
+    device tensor of shape (da + db + 1, s, s)."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A = _as_u32_tensor(A, dev)
+    B = _as_u32_tensor(B, dev)
+    da, db, s = A.shape[0] - 1, B.shape[0] - 1, A.shape[1]
+    need = ctypes.c_int64()
+    check(lib().polymat_mul_workspace(s, da, db, ctypes.byref(need)), "polymat_mul_workspace")
+    work = torch.empty(need.value, dtype=torch.uint8, device=dev)
+    C = torch.empty((da + db + 1, s, s), dtype=torch.int32, device=dev)
+    check(lib().polymat_mul(int(p), s, da, db, _ptr(A), _ptr(B), _ptr(C), _ptr(work), need.value,
+                            stream_ptr(stream)), "polymat_mul")
+    return C
+
+
 def spmv_check_status(h, stream=None):
     """Synchronise the stream; raise FFSPMVError (FFSPMV_ERR_TIMEOUT) if a
     bounded device wait of an earlier apply on h ran out."""
@@ -228,6 +246,6 @@ __all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
            "spmv_apply_transpose_noalloc",
            "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
            "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "spmv_check_status",
-           "spmv_apply_gf2", "stream_ptr",
+           "spmv_apply_gf2", "polymat_mul", "stream_ptr",
            "to_numpy_u32",
            "FFSPMVError", "Options"]

@@ -82,6 +82,10 @@ def _declare(L):
     L.spmv_check_status.restype = ctypes.c_int
     L.spmv_apply_gf2.argtypes = [_P, _I32, _P, _P, _I32, _I32, _P]
     L.spmv_apply_gf2.restype = ctypes.c_int
+    L.polymat_mul_workspace.argtypes = [_I32, _I64, _I64, ctypes.POINTER(_I64)]
+    L.polymat_mul_workspace.restype = ctypes.c_int
+    L.polymat_mul.argtypes = [_U32, _I32, _I64, _I64, _P, _P, _P, _P, _I64, _P]
+    L.polymat_mul.restype = ctypes.c_int
     for name, args, res in EXTRA_SIGNATURES:
         if hasattr(L, name):
             fn = getattr(L, name)
