@@ -14,7 +14,9 @@ Also printed, in the same JSON line:
   cpu_baseline  the CPU oracle on this host (bounded sample)
   clocks        SM clocks sampled during the timed region
   extra         other formats and moduli, the block Wiedemann sequence
-                (persistent kernel vs one launch per kernel), the batched launch
+                (persistent kernel vs one launch per kernel), the batched launch,
+                products over GF(2) with bit-packed vectors, and the
+                polynomial-matrix product of the sigma-basis step
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -53,7 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--modulus", type=int, default=65521)
     ap.add_argument("--format", default="AUTO")
-    ap.add_argument("--extras", default="formats,sequence",
+    ap.add_argument("--extras", default="formats,sequence,gf2,polymat",
                     help="comma list from formats,sequence,batch,gf2,polymat ('' for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default="",
