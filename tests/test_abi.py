@@ -17,7 +17,7 @@ def declared_functions():
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
             name = m.group(1)
-            if name.startswith(("spmv_", "ffspmv_")) and not name.endswith("_t"):
+            if name.startswith(("spmv_", "ffspmv_", "polymat_")) and not name.endswith("_t"):
                 names.add(name)
     return names
 
@@ -48,6 +48,16 @@ def test_host_side_argument_errors_without_gpu():
     assert L.spmv_apply(None, None, 1, None, 1, 1, 1, 0, None) == 1
     assert L.spmv_block_sequence(None, None, None, 16, 10, None, None, None) == 1
     assert L.spmv_batch_apply(-1, None, None, None, None, None) == 1
+    assert L.spmv_apply_gf2(None, 0, None, None, 1, 0, None) == 1
+    assert L.spmv_check_status(None, None) == 1
+    n = ctypes.c_int64()
+    assert L.polymat_mul_workspace(0, 1, 1, ctypes.byref(n)) == 1          # s >= 1
+    assert L.polymat_mul_workspace(33, 1, 1, ctypes.byref(n)) == 1         # s <= 32
+    assert L.polymat_mul_workspace(4, -1, 1, ctypes.byref(n)) == 1         # degrees >= 0
+    assert L.polymat_mul_workspace(4, 2**14, 2**14, ctypes.byref(n)) == 5  # length past 2^15
+    assert L.polymat_mul_workspace(16, 6250, 6250, ctypes.byref(n)) == 0
+    assert n.value == 3 * 3 * 256 * 16384 * 4 + 3 * 16384 * 4 + 256
+    assert L.polymat_mul(1, 4, 1, 1, None, None, None, None, 0, None) == 1  # p >= 2, pointers
     assert ff.status_string(6) == "device wait timed out"
     o = ff.options_default()
     assert o.use_pm1 == -1 and o.ell_width == -1 and o.transpose_mode == 0
