@@ -56,7 +56,7 @@ def test_host_side_argument_errors_without_gpu():
     assert L.polymat_mul_workspace(4, -1, 1, ctypes.byref(n)) == 1         # degrees >= 0
     assert L.polymat_mul_workspace(4, 2**14, 2**14, ctypes.byref(n)) == 5  # length past 2^15
     assert L.polymat_mul_workspace(16, 6250, 6250, ctypes.byref(n)) == 0
-    assert n.value == 3 * 3 * 256 * 16384 * 4 + 3 * 16384 * 4 + 256
+    assert n.value == 3 * 3 * 256 * 16384 * 4 + 3 * 16384 * 8 + 256
     assert L.polymat_mul(1, 4, 1, 1, None, None, None, None, 0, None) == 1  # p >= 2, pointers
     assert ff.status_string(6) == "device wait timed out"
     o = ff.options_default()
