@@ -1,6 +1,8 @@
 /*
  * Products of polynomial matrices over Z/pZ: the multiplication that the
- * sigma-basis / PM-Basis step of block Wiedemann (Sec. 3) is built from.
+ * sigma-basis / PM-Basis step of block Wiedemann is built from, computed by
+ * the evaluation / pointwise product / interpolation scheme of Sec. 3
+ * (parallel polynomial matrix multiplication).
  * C(x) = A(x) B(x) for s x s matrices whose entries are polynomials over
  * F_p.  Arrays are coefficient-major and row-major inside a coefficient:
  * A[k][i][j] (uint32, < p) is the coefficient of x^k in entry (i, j);

@@ -1,10 +1,14 @@
 // Products of s x s polynomial matrices over Z/pZ, C(x) = A(x) B(x): the
-// multiplication that the sigma-basis / PM-Basis step of block Wiedemann
-// (Sec. 3) is built from.  Coefficient-major arrays: A[k][i][j] is the
-// coefficient of x^k in entry (i, j).
+// multiplication that the sigma-basis / PM-Basis step of block Wiedemann is
+// built from, by the fast algorithm of Sec. 3 (parallel polynomial matrix
+// multiplication): evaluate both operands at the powers of a root of unity,
+// multiply the matrices point by point, interpolate back.  Coefficient-major
+// arrays: A[k][i][j] is the coefficient of x^k in entry (i, j).
 //
-// The exact integer coefficients of C are below s * min(da, db + ...) * (p-1)^2
-// < P0 P1 P2 for three NTT-friendly primes, so C is computed modulo each of
+// F_p itself has roots of unity of order at most 16 when p = 65521, so the
+// transforms run over three primes with large power-of-two roots instead: the
+// exact integer coefficients of C are below s * (min(da, db) + 1) * (p-1)^2
+// < P0 P1 P2, so C is computed modulo each of
 // them by number-theoretic transforms (length L, the power of two >= da+db+1;
 // one CTA per polynomial, in shared memory), a pointwise s x s matrix product
 // at each of the L points, and the inverse transforms, then brought back to
