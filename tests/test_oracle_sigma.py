@@ -1,0 +1,104 @@
+"""Pins of the sigma-basis oracle (oracle/sigma.py) to things other than
+itself: the approximant property and the determinant x^(sum of degree
+increases) for random inputs; the scalar case against Berlekamp-Massey
+(oracle/linalg.py); block Wiedemann's rank (deg det - codeg det of the
+minimal generator) against Gaussian elimination mod p on matrices of known
+rank; and M-Basis against PM-Basis."""
+import numpy as np
+import pytest
+
+from oracle import linalg, sigma
+
+P65521 = 65521
+
+
+def _rand_F(seed, d, m, n, p):
+    return np.random.default_rng(seed).integers(0, p, (d, m, n)).astype(object)
+
+
+@pytest.mark.parametrize("shift", [[0, 0, 0, 0], [2, 0, 1, 0]])
+def test_approximant_property_and_determinant(shift):
+    p, d = P65521, 9
+    F = _rand_F(1, d, 4, 2, p)
+    results = [sigma.mbasis(F, d, shift, p), sigma.pmbasis(F, d, shift, p, base=2)]
+    for P, delta in results:
+        for k in range(d):
+            assert not np.any(sigma.coeff(P, F, k, p)), k
+        grow = sum(a - b for a, b in zip(delta, shift))
+        assert grow == d * 2                  # generic F: two pivots at every order
+        dp = sigma.det_poly(P, p)
+        assert sigma.degree_and_codegree(dp) == (grow, grow)
+    assert sorted(results[0][1]) == sorted(results[1][1])
+
+
+@pytest.mark.parametrize("L", [1, 3, 6])
+def test_scalar_case_is_berlekamp_massey(L):
+    p = P65521
+    rng = np.random.default_rng(L)
+    c = [int(v) for v in rng.integers(1, p, L)]
+    s = [int(v) for v in rng.integers(0, p, L)]
+    N = 2 * L + 2
+    while len(s) < N:
+        s.append(sum(c[i] * s[-1 - i] for i in range(L)) % p)
+    C, LL = linalg.berlekamp_massey(s, p)
+    assert LL == L
+    F = np.zeros((N, 2, 1), dtype=object)
+    F[:, 0, 0] = s
+    F[0, 1, 0] = p - 1                                  # rows (u, v): u S - v = 0 mod x^N
+    for P, delta in (sigma.mbasis(F, N, [0, 0], p), sigma.pmbasis(F, N, [0, 0], p, base=2)):
+        r = int(np.argmin(delta))
+        assert delta[r] == L
+        u = [int(P[k, r, 0]) for k in range(P.shape[0])]
+        inv = pow(u[0], p - 2, p)
+        u = [v * inv % p for v in u]
+        while len(u) > 1 and u[-1] == 0:
+            u.pop()
+        assert u == list(C)
+
+
+def _inverse_mod(P, p):
+    n = len(P)
+    aug = [list(row) + [int(i == j) for j in range(n)] for i, row in enumerate(P)]
+    for c in range(n):
+        piv = next(i for i in range(c, n) if aug[i][c] % p)
+        aug[c], aug[piv] = aug[piv], aug[c]
+        inv = pow(aug[c][c], p - 2, p)
+        aug[c] = [(t * inv) % p for t in aug[c]]
+        for i in range(n):
+            if i != c and aug[i][c]:
+                f = aug[i][c]
+                aug[i] = [(t - f * w) % p for t, w in zip(aug[i], aug[c])]
+    return [row[n:] for row in aug]
+
+
+@pytest.mark.parametrize("p", [P65521, 2**31 - 1])
+def test_block_wiedemann_rank(p):
+    # A = Q diag(d_1..d_r, 0..0) Q^-1; S_i = X^T A^i Y; the s rows of least
+    # degree of an order-L sigma-basis of [S(x); -I] give the generator, and
+    # deg det - codeg det is the rank
+    n, s = 12, 3
+    rng = np.random.default_rng(5)
+    for r in (0, 4, 7, 11, 12):
+        while True:
+            Q = rng.integers(0, p, (n, n)).tolist()
+            if linalg.rank_mod_p(Q, p) == n:
+                break
+        dvals = rng.choice(np.arange(1, 10**4), r, replace=False).tolist() + [0] * (n - r)
+        D = [[dvals[i] if i == j else 0 for j in range(n)] for i in range(n)]
+        A = linalg.dense_matmul(linalg.dense_matmul(Q, D, p), _inverse_mod(Q, p), p)
+        assert linalg.rank_mod_p(A, p) == r
+        X = rng.integers(0, p, (n, s)).tolist()
+        V = rng.integers(0, p, (n, s)).tolist()
+        L = 2 * (n // s) + 4
+        F = np.zeros((L, 2 * s, s), dtype=object)
+        for i in range(L):
+            F[i, :s, :] = np.array([[sum(X[k][a] * V[k][b] for k in range(n)) % p for b in range(s)]
+                                    for a in range(s)], dtype=object)
+            V = linalg.dense_matmul(A, V, p)
+        for i in range(s):
+            F[0, s + i, i] = p - 1
+        P, delta = sigma.pmbasis(F, L, [0] * (2 * s), p, base=3)
+        rows = sorted(range(2 * s), key=lambda i: (delta[i], i))[:s]
+        dg, cdg = sigma.degree_and_codegree(sigma.det_poly(sigma.trim(P[:, rows, :s]), p))
+        assert dg - cdg == r, (r, delta)
+        assert dg == sum(delta[i] for i in rows)    # the generator is row reduced
