@@ -25,7 +25,8 @@ from ._lib import (FMT, SEL, TRANSPOSE, FFSPMVError, Options, lib,  # noqa: F401
 from ._api import (Matrix, spmv_apply, spmv_apply_transpose,  # noqa: F401
                    spmv_apply_transpose_noalloc,
                    spmv_batch_apply, spmv_block_sequence, spmv_create_hybrid,
-                   polymat_mul, spmv_apply_gf2, spmv_check_status, spmv_count_launches, spmv_describe_plan,
+                   polymat_mul, sigma_basis, sigma_wiedemann_input, spmv_apply_gf2, spmv_check_status,
+                   spmv_count_launches, spmv_describe_plan,
                    spmv_destroy, spmv_get_info, stream_ptr, to_numpy_u32)
 
 __all__ = ["build", "Matrix", "Options", "FMT", "SEL", "TRANSPOSE", "FFSPMVError",
@@ -33,7 +34,8 @@ __all__ = ["build", "Matrix", "Options", "FMT", "SEL", "TRANSPOSE", "FFSPMVError
            "spmv_apply_transpose_noalloc",
            "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
            "spmv_describe_plan", "spmv_get_info", "spmv_count_launches",
-           "spmv_check_status", "spmv_apply_gf2", "polymat_mul", "options_default", "to_numpy_u32",
+           "spmv_check_status", "spmv_apply_gf2", "polymat_mul", "sigma_basis", "sigma_wiedemann_input",
+           "options_default", "to_numpy_u32",
            "status_string", "library_path"]
 
 

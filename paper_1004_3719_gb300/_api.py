@@ -144,6 +144,42 @@ def polymat_mul(p, A, B, stream=None):
     return C
 
 
+def sigma_basis(p, F, shift=None, base=0, stream=None):
+    """Order-d sigma-basis of F, a coefficient-major (d, m, n) array of
+    residues (numpy uint32 or torch int32 on the device), d the order, for
+    the row shift `shift` (m integers, default 0); `base` is the largest
+    order handed to M-Basis (0 = the library's default).  Returns (P, delta,
+    degree): P a device tensor (d + 1, m, m), delta the m shifted row
+    degrees, degree an upper bound on deg P."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = _as_u32_tensor(F, dev)
+    d, m, n = F.shape
+    need = ctypes.c_int64()
+    check(lib().sigma_basis_workspace(m, n, d, int(base), ctypes.byref(need)), "sigma_basis_workspace")
+    work = torch.empty(need.value, dtype=torch.uint8, device=dev)
+    P = torch.empty((d + 1, m, m), dtype=torch.int32, device=dev)
+    sh = None if shift is None else np.ascontiguousarray(shift, dtype=np.int32)
+    delta = np.zeros(m, dtype=np.int32)
+    deg = ctypes.c_int64()
+    check(lib().sigma_basis(int(p), m, n, d, int(base), _ptr(F), _ptr(sh), _ptr(P), _ptr(delta),
+                            ctypes.byref(deg), _ptr(work), need.value, stream_ptr(stream)), "sigma_basis")
+    return P, [int(v) for v in delta], int(deg.value)
+
+
+def sigma_wiedemann_input(p, S, stream=None):
+    """[S(x); -I] as a (L, 2s, s) device tensor, from the (L, s, s) block
+    sequence S (device or numpy)."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    S = _as_u32_tensor(S, dev)
+    L, s = S.shape[0], S.shape[1]
+    F = torch.empty((L, 2 * s, s), dtype=torch.int32, device=dev)
+    check(lib().sigma_wiedemann_input(int(p), s, L, _ptr(S), _ptr(F), stream_ptr(stream)),
+          "sigma_wiedemann_input")
+    return F
+
+
 def spmv_check_status(h, stream=None):
     """Synchronise the stream; raise FFSPMVError (FFSPMV_ERR_TIMEOUT) if a
     bounded device wait of an earlier apply on h ran out."""
@@ -246,6 +282,6 @@ __all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
            "spmv_apply_transpose_noalloc",
            "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
            "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "spmv_check_status",
-           "spmv_apply_gf2", "polymat_mul", "stream_ptr",
+           "spmv_apply_gf2", "polymat_mul", "sigma_basis", "sigma_wiedemann_input", "stream_ptr",
            "to_numpy_u32",
            "FFSPMVError", "Options"]

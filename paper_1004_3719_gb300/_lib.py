@@ -86,6 +86,12 @@ def _declare(L):
     L.polymat_mul_workspace.restype = ctypes.c_int
     L.polymat_mul.argtypes = [_U32, _I32, _I64, _I64, _P, _P, _P, _P, _I64, _P]
     L.polymat_mul.restype = ctypes.c_int
+    L.sigma_basis_workspace.argtypes = [_I32, _I32, _I64, _I32, ctypes.POINTER(_I64)]
+    L.sigma_basis_workspace.restype = ctypes.c_int
+    L.sigma_basis.argtypes = [_U32, _I32, _I32, _I64, _I32, _P, _P, _P, _P, _P, _P, _I64, _P]
+    L.sigma_basis.restype = ctypes.c_int
+    L.sigma_wiedemann_input.argtypes = [_U32, _I32, _I64, _P, _P, _P]
+    L.sigma_wiedemann_input.restype = ctypes.c_int
     for name, args, res in EXTRA_SIGNATURES:
         if hasattr(L, name):
             fn = getattr(L, name)

@@ -17,7 +17,7 @@ def declared_functions():
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
             name = m.group(1)
-            if name.startswith(("spmv_", "ffspmv_", "polymat_")) and not name.endswith("_t"):
+            if name.startswith(("spmv_", "ffspmv_", "polymat_", "sigma_")) and not name.endswith("_t"):
                 names.add(name)
     return names
 
@@ -58,6 +58,15 @@ def test_host_side_argument_errors_without_gpu():
     assert L.polymat_mul_workspace(16, 6250, 6250, ctypes.byref(n)) == 0
     assert n.value == 3 * 3 * 256 * 16384 * 4 + 3 * 16384 * 8 + 256
     assert L.polymat_mul(1, 4, 1, 1, None, None, None, None, 0, None) == 1  # p >= 2, pointers
+    assert L.sigma_basis_workspace(33, 16, 10, 0, ctypes.byref(n)) == 1      # m <= 32
+    assert L.sigma_basis_workspace(8, 9, 10, 0, ctypes.byref(n)) == 1        # n <= m
+    assert L.sigma_basis_workspace(32, 32, 10, 32, ctypes.byref(n)) == 5     # leaf over shared memory
+    assert L.sigma_basis_workspace(32, 16, 30000, 0, ctypes.byref(n)) == 5   # products past 2^15 points
+    assert L.sigma_basis_workspace(32, 16, 12502, 0, ctypes.byref(n)) == 0
+    d = ctypes.c_int32(0)
+    assert L.sigma_basis(65521 * 3, 2, 1, 4, 0, 8, None, 8, ctypes.byref(d), None, 16, 1 << 20, None) == 1  # p prime
+    assert L.sigma_basis(65521, 2, 1, 4, 0, None, None, 8, ctypes.byref(d), None, 16, 1 << 20, None) == 1   # pointers
+    assert L.sigma_wiedemann_input(65521, 17, 4, 8, 8, None) == 1           # s <= 16
     assert ff.status_string(6) == "device wait timed out"
     o = ff.options_default()
     assert o.use_pm1 == -1 and o.ell_width == -1 and o.transpose_mode == 0
