@@ -47,11 +47,18 @@ struct SbLeaf {
 };
 
 // shared memory of one leaf: R (d x m x n), P ((d+1) x m x m), the column
-// operations (multipliers and addends, kSbMaxM x kSbMaxM each), pivots,
-// degrees, pivot flags, ranks, row scales and their inverses
+// operations (multiplier and addend pairs, kSbMaxM x kSbMaxM), pivots, degrees,
+// pivot flags and the inverse row scales
+// words before the op table: R and P, rounded up to an even count so that the
+// 8-byte pairs are aligned
+__host__ __device__ inline size_t sb_op_offset(int m, int n, long long d)
+{
+    return ((size_t)d * m * n + (size_t)(d + 1) * m * m + 1) & ~(size_t)1;
+}
+
 size_t sb_leaf_smem(int m, int n, long long d)
 {
-    return ((size_t)d * m * n + (size_t)(d + 1) * m * m + 2 * kSbMaxM * kSbMaxM + 7 * kSbMaxM) * 4;
+    return (sb_op_offset(m, n, d) + 2 * kSbMaxM * kSbMaxM + 4 * kSbMaxM) * 4;
 }
 
 __device__ u32 sb_pow(u32 a, u32 e, const Mod &M)
@@ -72,14 +79,11 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
     const u32 p = a.M.m;
     u32 *R = sb_sm;                                   // R[t][i][j] at (t m + i) n + j
     u32 *P = R + (size_t)d * m * n;                   // P[t][i][l] at (t m + i) m + l
-    u32 *sA = P + (size_t)(d + 1) * m * m;            // multiplier of row r at column j: sA[j][r]
-    u32 *sG = sA + kSbMaxM * kSbMaxM;                 // addend coefficient (times the pivot row)
-    int *spiv = (int *)(sG + kSbMaxM * kSbMaxM);      // pivot row of column j, -1 if none
+    uint2 *sop = reinterpret_cast<uint2 *>(sb_sm + sb_op_offset(m, n, d));  // (multiplier, addend) of row r at column j: sop[j][r]
+    int *spiv = (int *)(sop + kSbMaxM * kSbMaxM);     // pivot row of column j, -1 if none
     int *sdelta = spiv + kSbMaxM;
     int *sisp = sdelta + kSbMaxM;                     // row is a pivot at this order
-    int *srank = sisp + kSbMaxM;                      // position of row r in the order
-    u32 *scs = (u32 *)(srank + kSbMaxM);              // c_r: product of the multipliers of row r
-    u32 *sinv = scs + kSbMaxM;                        // 1 / c_r
+    u32 *sinv = (u32 *)(sisp + kSbMaxM);              // 1 / c_r
     const int tid = threadIdx.x;
 
     for (long long i = tid; i < (long long)d * m * n; i += blockDim.x) {
@@ -92,36 +96,37 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
     if (tid < m) {
         P[(size_t)tid * m + tid] = 1u;
         sdelta[tid] = a.shift[tid];
-        scs[tid] = 1u;
     }
     __syncthreads();
 
+    u32 cs = 1u;   // warp 0, lane r < m: c_r, the product of the multipliers applied to row r
     for (int k = 0; k < d; ++k) {
         if (tid < 32) {
-            // lane c holds column c of R_k (rows in registers, indexed by constants only)
+            // lane c holds column c of R_k; every lane holds the order positions
+            // of all rows; rows are indexed by constants only (registers)
             const int lane = tid;
-            if (lane < m) {
-                const int dl = sdelta[lane];
-                int rank = 0;   // position of the row in the order by (delta, index)
-                for (int j = 0; j < m; ++j) {
-                    const int dj = sdelta[j];
-                    rank += (dj < dl || (dj == dl && j < lane)) ? 1 : 0;
-                }
-                srank[lane] = rank;
+            const int dl = lane < m ? sdelta[lane] : INT_MAX;
+            int myrank = 0;   // position of row `lane` in the order by (delta, index)
+#pragma unroll
+            for (int j = 0; j < kSbMaxM; ++j) {
+                const int dj = __shfl_sync(0xffffffffu, dl, j);
+                myrank += (j < m && (dj < dl || (dj == dl && j < lane))) ? 1 : 0;
             }
-            __syncwarp();
+            int rk[kSbMaxM];
             u32 v[kSbMaxM];
 #pragma unroll
-            for (int r = 0; r < kSbMaxM; ++r)
+            for (int r = 0; r < kSbMaxM; ++r) {
+                rk[r] = __shfl_sync(0xffffffffu, myrank, r);
                 v[r] = (r < m && lane < n) ? R[((size_t)k * m + r) * n + lane] : 0u;
+            }
             u32 pivots = 0u;   // bit r: row r is a pivot at this order
             for (int j = 0; j < n; ++j) {
                 // lane j: the first row in the order, not yet a pivot, nonzero in column j
                 int best = 64, q = -1;
 #pragma unroll
                 for (int r = 0; r < kSbMaxM; ++r) {
-                    if (r < m && !((pivots >> r) & 1u) && v[r] != 0u && srank[r] < best) {
-                        best = srank[r];
+                    if (r < m && !((pivots >> r) & 1u) && v[r] != 0u && rk[r] < best) {
+                        best = rk[r];
                         q = r;
                     }
                 }
@@ -135,17 +140,18 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
 #pragma unroll
                 for (int r = 0; r < kSbMaxM; ++r) vq = (r == q) ? v[r] : vq;
                 const u32 av = __shfl_sync(0xffffffffu, vq, j);
+                u32 gmine = 0u;   // the addend coefficient of row `lane`
 #pragma unroll
                 for (int r = 0; r < kSbMaxM; ++r) {
                     const u32 br = __shfl_sync(0xffffffffu, v[r], j);
-                    const bool upd = r < m && !((pivots >> r) & 1u) && br != 0u && srank[r] > best;
-                    const u32 g = upd ? p - br : 0u;
+                    const bool upd = r < m && !((pivots >> r) & 1u) && br != 0u && rk[r] > best;
+                    const u32 g = upd ? p - br : 0u;   // nonzero exactly when row r is updated
                     if (upd && lane > j && lane < n) v[r] = red64((u64)av * v[r] + (u64)g * vq, a.M);
-                    if (lane == 0 && r < m) {
-                        sA[j * kSbMaxM + r] = upd ? av : 1u;
-                        sG[j * kSbMaxM + r] = g;
-                        if (upd) scs[r] = red64((u64)scs[r] * av, a.M);
-                    }
+                    gmine = (lane == r) ? g : gmine;
+                }
+                if (lane < m) {
+                    sop[j * kSbMaxM + lane] = make_uint2(gmine ? av : 1u, gmine);
+                    if (gmine) cs = red64((u64)cs * av, a.M);
                 }
                 pivots |= 1u << q;
                 if (lane == 0) spiv[j] = q;
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
             if (lane < m) {
                 const int ip = (pivots >> lane) & 1u;
                 sisp[lane] = ip;
-                if (ip) sdelta[lane] += 1;
+                if (ip) sdelta[lane] = dl + 1;
             }
         }
         __syncthreads();
@@ -182,8 +188,8 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
 #pragma unroll
                 for (int r = 0; r < kSbMaxM; ++r) {
                     if (r < m) {
-                        const u32 g = sG[j * kSbMaxM + r];
-                        if (g) v[r] = red64((u64)sA[j * kSbMaxM + r] * v[r] + (u64)g * vq, a.M);
+                        const uint2 op = sop[j * kSbMaxM + r];
+                        if (op.y) v[r] = red64((u64)op.x * v[r] + (u64)op.y * vq, a.M);
                     }
                 }
             }
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
         }
         __syncthreads();
     }
-    if (tid < m) sinv[tid] = sb_pow(scs[tid], p - 2u, a.M);   // c_r != 0 in the field F_p
+    if (tid < m) sinv[tid] = sb_pow(cs, p - 2u, a.M);   // c_r != 0 in the field F_p
     __syncthreads();
     for (long long i = tid; i < (long long)(d + 1) * m * m; i += blockDim.x) {
         const int r = (int)((i / m) % m);

@@ -35,6 +35,7 @@ def _gpu(lib, p, F, shift=None, base=0):
     (2**31 - 1, 6, 3, 37, 16, [2, 0, 1, 0, 3, 0], 1.0),
     (7, 8, 4, 30, 4, None, 0.3),                      # sparse, one zero column: orders without pivots
     (65521, 6, 6, 20, 4, None, 1.0),                  # n = m
+    (65521, 5, 3, 23, 3, [1, 0, 0, 2, 0], 1.0),       # odd m, n and leaf orders
     (65521, 32, 16, 20, 8, None, 1.0),                # the width of s = 16 block Wiedemann
     (65521, 32, 16, 32, 32, None, 1.0),               # one leaf of the largest order
     (1000003, 32, 32, 18, 16, None, 1.0),             # square, the default leaf order for it
