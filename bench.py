@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--modulus", type=int, default=65521)
     ap.add_argument("--format", default="AUTO")
-    ap.add_argument("--extras", default="formats,sequence,gf2,polymat",
-                    help="comma list from formats,sequence,batch,gf2,polymat ('' for none)")
+    ap.add_argument("--extras", default="formats,sequence,sigma,gf2,polymat",
+                    help="comma list from formats,sequence,sigma,batch,gf2,polymat ('' for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", default="",
                     help="'ax' or 'atx': only run warm-up + --steps launches of that product; "
@@ -328,6 +328,33 @@ def extra_sequence(torch, ff, stream):
     return res
 
 
+def extra_sigma(torch, ff, stream):
+    """The sigma-basis step of block Wiedemann on the 100k workload: the
+    12 502-term sequence S_i = X^T A^i Y (s = 16) from the GPU, then the
+    order-12 502 sigma-basis of [S(x); -I] (32 x 16), synchronous call."""
+    sp = stream.cuda_stream
+    p, s = 65521, 16
+    W = gen.wiedemann_matrix(seed=1003)
+    n = W.nrows
+    L = 2 * n // s + 2
+    X = torch.from_numpy(gen.uniform_block(1003, n, s, p).view(np.int32)).cuda()
+    Y = torch.from_numpy(gen.uniform_block(1003, n, s, p, key=1).view(np.int32)).cuda()
+    M = ff.Matrix.from_csr(W, transpose_mode=ff.TRANSPOSE.NONE)
+    S = M.block_sequence(X, Y, L, stream=sp)
+    F = ff.sigma_wiedemann_input(p, S, stream=sp)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        _, delta, deg = ff.sigma_basis(p, F, stream=sp)
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    rows = sorted(range(2 * s), key=lambda i: (delta[i], i))[:s]
+    return {"workload": f"sigma-basis of [S(x); -I], 32 x 16, order {L}, p={p} (100k Wiedemann sequence)",
+            "ms": round(min(ts), 1), "generator_row_degree_sum": sum(delta[i] for i in rows),
+            "basis_degree_bound": deg}
+
+
 def extra_batch(torch, ff, stream):
     sp = stream.cuda_stream
     probs = gen.batch_problems(seed=1004)
@@ -545,6 +572,7 @@ def main():
                      ("gf2", lambda: extra_gf2(torch, ff, flush, stream)),
                      ("formats", lambda: extra_formats(torch, ff, flush, stream)),
                      ("sequence", lambda: extra_sequence(torch, ff, stream)),
+                     ("sigma", lambda: extra_sigma(torch, ff, stream)),
                      ("batch", lambda: extra_batch(torch, ff, stream))):
         if name in wanted:
             try:
