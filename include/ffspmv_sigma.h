@@ -1,20 +1,21 @@
 /*
  * Sigma-bases (minimal approximant bases) over F_p: the second step of block
- * Wiedemann (Sec. 3, "Parallelization of the sigma-basis computation"), which
+ * Wiedemann (Sec. 3.2, "Parallelization of the sigma-basis computation"), which
  * turns the matrix sequence S_i = X^T A^i Y into a minimal matrix generator.
  * The algorithm is PM-Basis of Giorgi, Jeannerod and Villard (ISSAC 2003):
  * divide and conquer on the order, reduced to polynomial-matrix products
  * (polymat_mul, the evaluation / pointwise product / interpolation scheme of
- * Sec. 3), with their iterative M-Basis at small orders, as Sec. 3 recommends.
+ * Sec. 3.2.1), with their iterative M-Basis at small orders, as Sec. 3.2.2
+ * recommends.
  *
  * Definitions.  F in F_p[x]^{m x n}, an order d >= 1 and a shift s in Z^m.
  * An order-d sigma-basis of F is an m x m polynomial matrix P whose rows
  * generate every approximant v (a row vector with v F = 0 mod x^d) and have
  * minimal s-shifted degrees; delta_i = s_i + the number of times row i was
  * multiplied by x, and deg P_ij <= delta_i - s_j.  For block Wiedemann,
- * F = [S(x); -I_s] (m = 2s, n = s, s = 0); the s rows of P with the smallest
+ * F = [S(x); -I_s] (m = 2s, n = s, zero shift); the s rows of P with the smallest
  * delta (first s columns) give the minimal generator, and deg det - codeg det
- * of that generator is the rank of a suitably preconditioned A.
+ * of that generator (Sec. 3.3) is the rank of a suitably preconditioned A.
  *
  * Layout: polynomial matrices are coefficient-major and row-major inside a
  * coefficient, uint32 residues: F[k][i][j] is the coefficient of x^k in entry

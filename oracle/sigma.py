@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring): the tests are the only
 callers.
 
-Block Wiedemann's second step (Sec. 3) computes the minimal matrix generator
+Block Wiedemann's second step (Sec. 3.2) computes the minimal matrix generator
 of the sequence S_i by a sigma-basis computation, with the algorithm PM-Basis
 of Giorgi, Jeannerod and Villard (2003), which reduces to polynomial-matrix
 products and, at small orders, to their iterative M-Basis.  Definitions used

@@ -1,9 +1,9 @@
-// Sigma-bases over F_p for the second step of block Wiedemann (Sec. 3,
+// Sigma-bases over F_p for the second step of block Wiedemann (Sec. 3.2,
 // "Parallelization of the sigma-basis computation"): PM-Basis (Giorgi,
 // Jeannerod and Villard, ISSAC 2003) as a host recursion on the order whose
-// work is polynomial-matrix products on the GPU (polymat_mul, Sec. 3's
+// work is polynomial-matrix products on the GPU (polymat_mul, Sec. 3.2.1's
 // evaluation / pointwise / interpolation scheme), and M-Basis, the iterative
-// algorithm Sec. 3 recommends at small orders, as one CTA per leaf.
+// algorithm Sec. 3.2.2 recommends at small orders, as one CTA per leaf.
 //
 // M-Basis leaf.  For an order-d problem (d <= 32) the CTA keeps in shared
 // memory the residual R = P F (coefficients k..d-1, m x n each) and the basis
