@@ -102,3 +102,45 @@ def test_block_wiedemann_rank(p):
         dg, cdg = sigma.degree_and_codegree(sigma.det_poly(sigma.trim(P[:, rows, :s]), p))
         assert dg - cdg == r, (r, delta)
         assert dg == sum(delta[i] for i in rows)    # the generator is row reduced
+
+
+def _count_approximants(F, d, shift, D, p):
+    """Brute force: how many row vectors v with deg v_i <= D - s_i satisfy
+    v F = 0 mod x^d (every vector enumerated, no algebra)."""
+    import itertools
+    m, n = F.shape[1], F.shape[2]
+    sizes = [max(0, D - s + 1) for s in shift]
+    count = 0
+    for flat in itertools.product(range(p), repeat=sum(sizes)):
+        coeffs, pos = [], 0
+        for sz in sizes:
+            coeffs.append(flat[pos:pos + sz])
+            pos += sz
+        ok = True
+        for k in range(d):
+            for j in range(n):
+                acc = 0
+                for i in range(m):
+                    for t, c in enumerate(coeffs[i]):
+                        if c and k - t >= 0 and k - t < F.shape[0]:
+                            acc += c * int(F[k - t, i, j])
+                if acc % p:
+                    ok = False
+                    break
+            if not ok:
+                break
+        count += ok
+    return count
+
+
+@pytest.mark.parametrize("p,m,n,d,shift,seed", [(3, 2, 1, 5, [0, 0], 1), (2, 3, 1, 4, [0, 1, 0], 2),
+                                                (2, 3, 2, 3, [0, 0, 0], 3), (3, 3, 2, 2, [1, 0, 0], 4)])
+def test_degrees_are_minimal_by_enumeration(p, m, n, d, shift, seed):
+    # a reduced basis has the predictable-degree property: the approximants of
+    # shifted degree <= D form a space of dimension sum_i max(0, D - delta_i + 1);
+    # counting them one by one pins the degrees without the algorithm
+    F = np.random.default_rng(seed).integers(0, p, (d, m, n)).astype(object)
+    for P, delta in (sigma.mbasis(F, d, shift, p), sigma.pmbasis(F, d, shift, p, base=1)):
+        for D in range(0, 3):
+            want = p ** sum(max(0, D - dl + 1) for dl in delta)
+            assert _count_approximants(F, d, shift, D, p) == want, (D, delta)
