@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--profile", default="",
                     help="'ax' or 'atx': only run warm-up + --steps launches of that product; "
                          "'seq': one block sequence of --steps steps on the 100k Wiedemann "
-                         "matrix (no timing, no extras), for an ncu capture")
+                         "matrix; 'polymat': three 16 x 16 polynomial-matrix products of degree "
+                         "6250; 'sigma': one sigma-basis of [S(x); -I] for a uniform 16 x 16 "
+                         "sequence of --steps terms (no timing, no extras), for an ncu capture")
     return ap.parse_args()
 
 
@@ -456,6 +458,22 @@ def main():
     torch.cuda.set_device(local)
     import paper_1004_3719_gb300 as ff
     ff.build()
+    if args.profile == "polymat":
+        p, s, d = 65521, 16, 6250
+        A = gen.uniform_block(21, (d + 1) * s, s, p).reshape(d + 1, s, s)
+        B = gen.uniform_block(22, (d + 1) * s, s, p).reshape(d + 1, s, s)
+        for _ in range(3):
+            ff.polymat_mul(p, A, B)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "polymat", "products": 3}))
+        return
+    if args.profile == "sigma":
+        p, s = 65521, 16
+        S = gen.uniform_block(23, args.steps * s, s, p).reshape(args.steps, s, s)
+        _, delta, deg = ff.sigma_basis(p, ff.sigma_wiedemann_input(p, S))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "sigma", "order": args.steps, "delta_sum": sum(delta), "degree_bound": deg}))
+        return
     if args.profile == "seq":
         W = gen.wiedemann_matrix(seed=1003)
         X = torch.from_numpy(gen.uniform_block(1003, W.nrows, 16, 65521).view(np.int32)).cuda()
