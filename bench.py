@@ -354,7 +354,8 @@ def extra_sigma(torch, ff, stream):
     rows = sorted(range(2 * s), key=lambda i: (delta[i], i))[:s]
     return {"workload": f"sigma-basis of [S(x); -I], 32 x 16, order {L}, p={p} (100k Wiedemann sequence)",
             "ms": round(min(ts), 1), "generator_row_degree_sum": sum(delta[i] for i in rows),
-            "basis_degree_bound": deg}
+            "basis_degree_bound": deg,
+            "degrees_sum_to_s_L": sum(delta) == s * L}  # det P = c x^(s L) for [S; -I]
 
 
 def extra_batch(torch, ff, stream):
