@@ -55,9 +55,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--modulus", type=int, default=65521)
     ap.add_argument("--format", default="AUTO")
-    ap.add_argument("--extras", default="formats,sequence,sigma,gf2,polymat",
-                    help="comma list from formats,sequence,sigma,batch,gf2,polymat ('' for none)")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--extras", default="formats,multivec,batch,sequence,sigma,gf2,polymat",
+                    help="comma list from formats,multivec,batch,sequence,sigma,gf2,polymat "
+                         "('' for none)")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0,
+                    help="seconds of oracle work for each of the single-thread and all-core "
+                         "CPU baselines")
     ap.add_argument("--profile", default="",
                     help="'ax' or 'atx': only run warm-up + --steps launches of that product; "
                          "'seq': one block sequence of --steps steps on the 100k Wiedemann "
@@ -131,11 +134,14 @@ class Clocks:
 
 
 def algorithmic_bytes(A, m):
-    """Sec. 2.1 CSR traffic of one y = A*x: per nonzero a 4-byte column index
-    and a value (2 bytes if m <= 2^16, 4 otherwise), plus 4(n+1) bytes of row
-    pointers, 4n of x and 4n of y."""
+    """Sec. 2.1 CSR traffic of one y = A*x with the +-1 entries value-free
+    (Sec. 2.4.2): per nonzero a 4-byte column index, plus a value (2 bytes if
+    m <= 2^16, 4 otherwise) unless the entry is +1 or -1 (value 1 or m - 1),
+    plus 4(n+1) bytes of row pointers, 4n of x and 4n of y."""
     vb = 2 if m <= 65536 else 4
-    return A.nnz * (4 + vb) + 4 * (A.nrows + 1) + 4 * A.ncols + 4 * A.nrows
+    v = np.asarray(A.val, dtype=np.uint64) % m
+    general = int(A.nnz - np.count_nonzero((v == 1) | (v == m - 1)))
+    return 4 * A.nnz + vb * general + 4 * (A.nrows + 1) + 4 * A.ncols + 4 * A.nrows
 
 
 def traffic_record(kernel_key):
@@ -159,22 +165,40 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(A, x, seconds):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_steps(A, x, seconds, threads):
     """The oracle's y = A x and z = A^T x on this host, repeated for about
-    `seconds` (at least once)."""
+    `seconds` (at least once) on `threads` host threads (rows split
+    statically); returns (steps, seconds)."""
     import oracle
     n = 0
     t0 = time.perf_counter()
     while True:
-        oracle.csr_spmv(A, x)
-        oracle.csr_spmv_transpose(A, x)
+        oracle.csr_spmv(A, x, threads=threads)
+        oracle.csr_spmv_transpose(A, x, threads=threads)
         n += 1
         if time.perf_counter() - t0 >= seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": round(2 * A.nnz * n / dt / 1e9, 4), "unit": UNIT, "cores": 1,
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(A, x, seconds):
+    """The oracle on all host cores (the reported baseline) and on one."""
+    cores = host_cores()
+    n1, t1 = oracle_steps(A, x, seconds, 1)
+    nc, tc = oracle_steps(A, x, seconds, cores)
+    return {"value": round(2 * A.nnz * nc / tc / 1e9, 4), "unit": UNIT, "cores": cores,
             "kind": "oracle",
-            "sample": f"{n} steps (y=A*x, z=A^T*x) on the full matrix, single thread, {dt:.1f} s"}
+            "sample": f"{nc} steps (y=A*x, z=A^T*x) on the full matrix, rows split over "
+                      f"{cores} threads, {tc:.1f} s",
+            "single_thread": {"value": round(2 * A.nnz * n1 / t1 / 1e9, 4), "cores": 1,
+                              "sample": f"{n1} steps, one thread, {t1:.1f} s"}}
 
 
 def shard(count, rank, world):
@@ -213,13 +237,14 @@ def run_reference(args):
     oracle.build()
     A = gen.powerlaw_matrix(seed=SEED, m=args.modulus)
     x = gen.uniform_block(SEED, A.ncols, 1, args.modulus)
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle.csr_spmv(A, x)
-        oracle.csr_spmv_transpose(A, x)
+        oracle.csr_spmv(A, x, threads=cores)
+        oracle.csr_spmv_transpose(A, x, threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.csr_spmv(A, x)
-        oracle.csr_spmv_transpose(A, x)
+        oracle.csr_spmv(A, x, threads=cores)
+        oracle.csr_spmv_transpose(A, x, threads=cores)
     dt = time.perf_counter() - t0
     val = 2 * A.nnz * args.steps / dt / 1e9
     print(json.dumps({
@@ -228,8 +253,9 @@ def run_reference(args):
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "modulus": args.modulus},
-        "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} timed steps of the full workload, single thread"},
+        "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} timed steps of the full workload, rows split "
+                                   f"over {cores} threads"},
         "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
 
@@ -312,14 +338,14 @@ def extra_sequence(torch, ff, stream):
     for mode, name in ((0, "persistent_graph"), (1, "per_launch")):
         M = ff.Matrix.from_csr(W, sequence_mode=mode, transpose_mode=ff.TRANSPOSE.NONE)
         S = torch.empty((L, s, s), dtype=torch.int32, device="cuda")
-        ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, sp)
+        ff.spmv_block_sequence(M.handle, X, Y, s, 0, L, S, None, sp)
         torch.cuda.synchronize()
         ts = []
         for _ in range(3 if mode == 0 else 1):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ff.spmv_block_sequence(M.handle, X, Y, s, L, S, None, sp)
+            ff.spmv_block_sequence(M.handle, X, Y, s, 0, L, S, None, sp)
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))

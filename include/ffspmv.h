@@ -138,20 +138,28 @@ ffspmv_status spmv_apply_transpose(ffspmv_t h, const uint32_t *d_x,
 /*
  * The matrix sequence of block Wiedemann (Sec. 3, step 1, with independent
  * left and right projections): V_0 = Y, V_{i+1} = A*V_i (mod p) and
- * S_i = X^T * V_i (mod p) for 0 <= i < nsteps, all kept on the device
- * (Sec. 2.5.2).  A must be square; p is the handle's modulus.
- * d_X, d_Y: n x s row-major (ld = s), 1 <= s <= 32.  d_S: nsteps x s x s,
- * S_i[a][b] at d_S[(i*s + a)*s + b].  d_V_next: NULL, or n x s receiving
- * A^nsteps * Y, from which a later call continues the sequence (checkpoint /
- * resume).  The steps run as one persistent cooperative kernel captured in a
- * CUDA graph when the grid fits on the device, else as one graph of
- * per-step launches.  Synchronises `stream` and returns
- * FFSPMV_ERR_TIMEOUT if a bounded grid-barrier wait expired.
+ * S_i = X^T * V_i (mod p), all kept on the device (Sec. 2.5.2).  This call
+ * computes the nsteps blocks S_start_step .. S_{start_step+nsteps-1}.  A must
+ * be square; p is the handle's modulus.  d_X, d_Y: n x s row-major (ld = s),
+ * 1 <= s <= 32.  d_S: nsteps x s x s, S_{start_step+i}[a][b] at
+ * d_S[(i*s + a)*s + b].
+ * d_V_state: n x s, in/out, for checkpoint and resume.  With start_step = 0
+ * it may be NULL; if given it receives V_nsteps = A^nsteps * Y.  With
+ * start_step > 0 it is required: on entry it holds V_start_step (what an
+ * earlier call left there), d_Y is not read (may be NULL), and on return it
+ * holds V_{start_step+nsteps}.  The steps run as one persistent cooperative
+ * kernel captured in a CUDA graph when the grid fits on the device, else as
+ * one stream of per-step launches; the graph is kept on the handle and
+ * re-captured when s, nsteps, d_X, d_Y (or d_V_state), d_S change.
+ * Synchronises `stream` and returns FFSPMV_ERR_TIMEOUT if a bounded
+ * grid-barrier wait expired.  FFSPMV_ERR_ARG: start_step < 0, nsteps < 0,
+ * s outside [1, 32], A not square, a missing pointer.
  */
 ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X,
                                   const uint32_t *d_Y, int32_t s,
-                                  int64_t nsteps, uint32_t *d_S,
-                                  uint32_t *d_V_next, ffspmv_stream_t stream);
+                                  int64_t start_step, int64_t nsteps,
+                                  uint32_t *d_S, uint32_t *d_V_state,
+                                  ffspmv_stream_t stream);
 
 /*
  * Independent products Y_j = A_j * X_j (mod m_j), j < count, in one launch
@@ -181,7 +189,10 @@ ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
  * exits; ncols * min(nvec, 16) must fit in it, so ncols <= 2^20 (larger
  * ncols: FFSPMV_ERR_UNSUPPORTED; wider blocks are done 2^20/ncols vectors at
  * a time).  h must have been created with FFSPMV_TRANSPOSE_ATOMIC (else
- * FFSPMV_ERR_UNSUPPORTED).  The first call on a device, with that device
+ * FFSPMV_ERR_UNSUPPORTED), and h's device must be the current device (else
+ * FFSPMV_ERR_ARG).  A handle created with value_check = 1 gets the same
+ * input check as spmv_apply_transpose (FFSPMV_ERR_RANGE when some x >= m;
+ * that check synchronises `stream`).  The first call on a device, with that device
  * current, looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the array and
  * each clears the part it uses: calls whose work overlaps on the GPU (other

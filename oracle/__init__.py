@@ -33,7 +33,7 @@ def build(force=False):
                  os.path.getmtime(_LIB) < os.path.getmtime(_SRC))
         if force or stale:
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+            subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
                             "-o", tmp, _SRC], check=True)
             os.replace(tmp, _LIB)
     return _LIB
@@ -54,6 +54,9 @@ def _load():
         lib.oracle_block_sequence.argtypes = [i64, p, p, p, u32, p, p, i32,
                                               i64, p, p]
         lib.oracle_block_sequence.restype = ctypes.c_int
+        for f in (lib.oracle_spmv_threads, lib.oracle_spmv_transpose_threads):
+            f.argtypes = [i32] + sig
+            f.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -76,25 +79,27 @@ def _block(x, rows):
     return x
 
 
-def spmv(nrows, ncols, row_ptr, col, val, m, x, y=None, alpha=1, beta=0):
+def spmv(nrows, ncols, row_ptr, col, val, m, x, y=None, alpha=1, beta=0, threads=1):
     """y <- alpha*A*x + beta*y mod m (Sec. 2).  ``x`` is ncols or
-    ncols x nvec; returns a new array shaped like ``x`` with nrows rows."""
+    ncols x nvec; returns a new array shaped like ``x`` with nrows rows.
+    ``threads`` > 1 splits the rows over that many host threads (timing)."""
     row_ptr, col, val = _csr_arrays(row_ptr, col, val)
     flat = np.asarray(x).ndim == 1
     xb = _block(x, ncols)
     nvec = xb.shape[1]
     out = (np.zeros((nrows, nvec), dtype=np.uint32) if y is None else
            _block(np.array(y, dtype=np.uint32, copy=True), nrows))
-    rc = _load().oracle_spmv(nrows, ncols, _ptr(row_ptr), _ptr(col), _ptr(val),
-                             m, _ptr(xb), nvec, _ptr(out), nvec, nvec,
-                             alpha % m, beta % m)
+    args = (nrows, ncols, _ptr(row_ptr), _ptr(col), _ptr(val), m, _ptr(xb), nvec,
+            _ptr(out), nvec, nvec, alpha % m, beta % m)
+    rc = (_load().oracle_spmv(*args) if threads <= 1 else
+          _load().oracle_spmv_threads(int(threads), *args))
     if rc != 0:
         raise ValueError(f"oracle_spmv failed ({rc})")
     return out.reshape(nrows) if flat else out
 
 
 def spmv_transpose(nrows, ncols, row_ptr, col, val, m, x, y=None, alpha=1,
-                   beta=0):
+                   beta=0, threads=1):
     """y <- alpha*A^T*x + beta*y mod m.  ``x`` has nrows rows, the result
     ncols rows."""
     row_ptr, col, val = _csr_arrays(row_ptr, col, val)
@@ -103,9 +108,10 @@ def spmv_transpose(nrows, ncols, row_ptr, col, val, m, x, y=None, alpha=1,
     nvec = xb.shape[1]
     out = (np.zeros((ncols, nvec), dtype=np.uint32) if y is None else
            _block(np.array(y, dtype=np.uint32, copy=True), ncols))
-    rc = _load().oracle_spmv_transpose(nrows, ncols, _ptr(row_ptr), _ptr(col),
-                                       _ptr(val), m, _ptr(xb), nvec, _ptr(out),
-                                       nvec, nvec, alpha % m, beta % m)
+    args = (nrows, ncols, _ptr(row_ptr), _ptr(col), _ptr(val), m, _ptr(xb), nvec,
+            _ptr(out), nvec, nvec, alpha % m, beta % m)
+    rc = (_load().oracle_spmv_transpose(*args) if threads <= 1 else
+          _load().oracle_spmv_transpose_threads(int(threads), *args))
     if rc != 0:
         raise ValueError(f"oracle_spmv_transpose failed ({rc})")
     return out.reshape(ncols) if flat else out

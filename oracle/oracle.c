@@ -18,6 +18,7 @@
  *
  * Return value: 0 on success, -1 on a bad argument, -2 when out of memory.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -157,4 +158,125 @@ int oracle_block_sequence(int64_t n, const int64_t *row_ptr, const int32_t *col,
     free(V);
     free(W);
     return rc;
+}
+
+/*
+ * The same two products on several host threads, for timing the oracle on
+ * all cores.  Rows are split into `nthreads` contiguous blocks (a static row
+ * partition); each thread evaluates the plain definition above on its
+ * block, unchanged.  For A*x the blocks write disjoint rows of y.  For A^T*x
+ * each thread forms the definition's sum over its rows only (its own
+ * partial column sums, reduced mod m), and the partial sums are then added
+ * exactly and combined with alpha and beta once per output.
+ */
+struct job {
+    int64_t r0, r1, ncols;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const uint32_t *val;
+    uint32_t m;
+    const uint32_t *x;
+    int64_t ldx;
+    uint32_t *y;
+    int64_t ldy;
+    int32_t nvec;
+    uint32_t alpha, beta;
+    int transpose, rc;
+};
+
+static void *run_job(void *arg)
+{
+    struct job *j = (struct job *)arg;
+    if (j->transpose)
+        j->rc = oracle_spmv_transpose(j->r1 - j->r0, j->ncols, j->row_ptr + j->r0, j->col,
+                                      j->val, j->m, j->x + j->r0 * j->ldx, j->ldx, j->y,
+                                      j->ldy, j->nvec, 1, 0);
+    else
+        j->rc = oracle_spmv(j->r1 - j->r0, j->ncols, j->row_ptr + j->r0, j->col, j->val,
+                            j->m, j->x, j->ldx, j->y + j->r0 * j->ldy, j->ldy, j->nvec,
+                            j->alpha, j->beta);
+    return 0;
+}
+
+static int run_threads(int nthreads, int transpose, int64_t nrows, int64_t ncols,
+                       const int64_t *row_ptr, const int32_t *col, const uint32_t *val,
+                       uint32_t m, const uint32_t *x, int64_t ldx, uint32_t *y, int64_t ldy,
+                       int32_t nvec, uint32_t alpha, uint32_t beta)
+{
+    if (bad_common(nrows, row_ptr, m, ldx, ldy, nvec) || ncols < 0 || nthreads < 1)
+        return -1;
+    if (nthreads > 256)
+        nthreads = 256;
+    struct job jobs[256];
+    pthread_t tid[256];
+    uint32_t *part = 0;
+    if (transpose) {
+        part = (uint32_t *)calloc((size_t)nthreads * (size_t)(ncols > 0 ? ncols : 1) * nvec,
+                                  sizeof(uint32_t));
+        if (!part)
+            return -2;
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        struct job *j = &jobs[t];
+        j->r0 = nrows * t / nthreads;
+        j->r1 = nrows * (t + 1) / nthreads;
+        j->ncols = ncols;
+        j->row_ptr = row_ptr;
+        j->col = col;
+        j->val = val;
+        j->m = m;
+        j->x = x;
+        j->ldx = ldx;
+        j->y = transpose ? part + (size_t)t * (size_t)ncols * nvec : y;
+        j->ldy = transpose ? nvec : ldy;
+        j->nvec = nvec;
+        j->alpha = alpha;
+        j->beta = beta;
+        j->transpose = transpose;
+        j->rc = 0;
+    }
+    int started = 0;
+    for (; started < nthreads; ++started)
+        if (pthread_create(&tid[started], 0, run_job, &jobs[started]) != 0)
+            break;
+    for (int t = started; t < nthreads; ++t)
+        run_job(&jobs[t]);  /* threads that could not start run here */
+    for (int t = 0; t < started; ++t)
+        pthread_join(tid[t], 0);
+    int rc = 0;
+    for (int t = 0; t < nthreads; ++t)
+        if (jobs[t].rc != 0)
+            rc = jobs[t].rc;
+    if (transpose && rc == 0) {
+        for (int64_t jj = 0; jj < ncols; ++jj) {
+            for (int32_t v = 0; v < nvec; ++v) {
+                u128 acc = 0;
+                for (int t = 0; t < nthreads; ++t)
+                    acc += part[((size_t)t * ncols + jj) * nvec + v];
+                u128 r = (u128)alpha * (acc % m) + (u128)beta * y[jj * ldy + v];
+                y[jj * ldy + v] = (uint32_t)(r % m);
+            }
+        }
+    }
+    free(part);
+    return rc;
+}
+
+int oracle_spmv_threads(int32_t nthreads, int64_t nrows, int64_t ncols,
+                        const int64_t *row_ptr, const int32_t *col, const uint32_t *val,
+                        uint32_t m, const uint32_t *x, int64_t ldx, uint32_t *y,
+                        int64_t ldy, int32_t nvec, uint32_t alpha, uint32_t beta)
+{
+    return run_threads(nthreads, 0, nrows, ncols, row_ptr, col, val, m, x, ldx, y, ldy,
+                       nvec, alpha, beta);
+}
+
+int oracle_spmv_transpose_threads(int32_t nthreads, int64_t nrows, int64_t ncols,
+                                  const int64_t *row_ptr, const int32_t *col,
+                                  const uint32_t *val, uint32_t m, const uint32_t *x,
+                                  int64_t ldx, uint32_t *y, int64_t ldy, int32_t nvec,
+                                  uint32_t alpha, uint32_t beta)
+{
+    return run_threads(nthreads, 1, nrows, ncols, row_ptr, col, val, m, x, ldx, y, ldy,
+                       nvec, alpha, beta);
 }

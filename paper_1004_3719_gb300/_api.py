@@ -79,9 +79,9 @@ def spmv_apply_transpose_noalloc(h, x, ldx, y, ldy, nvec, alpha=1, beta=0, strea
           "spmv_apply_transpose_noalloc")
 
 
-def spmv_block_sequence(h, X, Y, s, nsteps, S, V_next=None, stream=None):
-    check(lib().spmv_block_sequence(h, _ptr(X), _ptr(Y), int(s), int(nsteps), _ptr(S),
-                                    _ptr(V_next), stream_ptr(stream)),
+def spmv_block_sequence(h, X, Y, s, start_step, nsteps, S, V_state=None, stream=None):
+    check(lib().spmv_block_sequence(h, _ptr(X), _ptr(Y), int(s), int(start_step), int(nsteps),
+                                    _ptr(S), _ptr(V_state), stream_ptr(stream)),
           "spmv_block_sequence")
 
 
@@ -261,7 +261,9 @@ class Matrix:
         return y
 
     def block_sequence(self, X, Y, nsteps, want_next=False, stream=None):
-        """S_i = X^T A^i Y (mod m), 0 <= i < nsteps; X, Y: n x s."""
+        """S_i = X^T A^i Y (mod m), 0 <= i < nsteps; X, Y: n x s.  With
+        want_next, also returns V_nsteps = A^nsteps Y (the state from which
+        `resume_sequence` continues)."""
         torch = _torch()
         dev = torch.device("cuda", torch.cuda.current_device())
         X = _as_u32_tensor(X, dev)
@@ -269,8 +271,20 @@ class Matrix:
         s = X.shape[1] if X.dim() == 2 else 1
         S = torch.empty((max(int(nsteps), 0), s, s), dtype=torch.int32, device=dev)
         Vn = torch.empty((self.nrows, s), dtype=torch.int32, device=dev) if want_next else None
-        spmv_block_sequence(self.handle, X, Y, s, nsteps, S, Vn, stream)
+        spmv_block_sequence(self.handle, X, Y, s, 0, nsteps, S, Vn, stream)
         return (S, Vn) if want_next else S
+
+    def resume_sequence(self, X, V_state, start_step, nsteps, stream=None):
+        """S_start_step .. S_{start_step+nsteps-1}, continuing from V_state =
+        V_start_step (a device tensor, n x s), which is advanced in place to
+        V_{start_step+nsteps}."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        X = _as_u32_tensor(X, dev)
+        s = X.shape[1] if X.dim() == 2 else 1
+        S = torch.empty((max(int(nsteps), 0), s, s), dtype=torch.int32, device=dev)
+        spmv_block_sequence(self.handle, X, None, s, start_step, nsteps, S, V_state, stream)
+        return S
 
 
 def to_numpy_u32(t):

@@ -62,7 +62,7 @@ def _declare(L):
     for f in (L.spmv_apply, L.spmv_apply_transpose):
         f.argtypes = [_P, _P, _I64, _P, _I64, _I32, _U32, _U32, _P]
         f.restype = ctypes.c_int
-    L.spmv_block_sequence.argtypes = [_P, _P, _P, _I32, _I64, _P, _P, _P]
+    L.spmv_block_sequence.argtypes = [_P, _P, _P, _I32, _I64, _I64, _P, _P, _P]
     L.spmv_block_sequence.restype = ctypes.c_int
     L.spmv_batch_apply.argtypes = [_I32, _P, _P, _P, _P, _P]
     L.spmv_batch_apply.restype = ctypes.c_int

@@ -218,6 +218,11 @@ struct BatchCache {
     int nitems = 0;
     std::vector<int> chunk_item0;
     int shape = -1;
+    // recorded on the stream of the last launch; the work list is not
+    // overwritten before it completes (a launch on another stream may still
+    // be reading it)
+    cudaEvent_t done = nullptr;
+    bool pending = false;
 };
 
 BatchCache g_cache;
@@ -307,6 +312,10 @@ WorkList make_items(const std::vector<ffspmv_handle *> &hs, const std::vector<BM
 
 ffspmv_status upload_items(BatchCache &C, const WorkList &W, int count)
 {
+    if (C.pending) {
+        FF_CUDA(cudaEventSynchronize(C.done));
+        C.pending = false;
+    }
     const size_t bm = (sizeof(BMat) * count + 255) / 256 * 256;
     const size_t need = bm + sizeof(BItem) * std::max<size_t>(W.items.size(), 1) + 256;
     if (need > C.dev_bytes) {
@@ -327,7 +336,7 @@ ffspmv_status upload_items(BatchCache &C, const WorkList &W, int count)
     return FFSPMV_OK;
 }
 
-ffspmv_status launch(const BatchCache &C, int count, const uint32_t *const *d_x,
+ffspmv_status launch(BatchCache &C, int count, const uint32_t *const *d_x,
                      uint32_t *const *d_y, cudaStream_t st)
 {
     for (int c = 0; c * kMaxBatch < count; ++c) {
@@ -343,6 +352,8 @@ ffspmv_status launch(const BatchCache &C, int count, const uint32_t *const *d_x,
                                                                 c * kMaxBatch, P);
         FF_CUDA(cudaGetLastError());
     }
+    FF_CUDA(cudaEventRecord(C.done, st));
+    C.pending = true;
     return FFSPMV_OK;
 }
 
@@ -371,6 +382,7 @@ extern "C" ffspmv_status spmv_batch_apply(int32_t count, const ffspmv_t *hs,
     if (count == 0) return FFSPMV_OK;
     cudaStream_t st = (cudaStream_t)stream;
     BatchCache &C = g_cache;
+    if (!C.done) FF_CUDA(cudaEventCreateWithFlags(&C.done, cudaEventDisableTiming));
     for (int j = 0; j < count; ++j) {
         if (!hs[j] || nvec[j] < 1 || nvec[j] > 32) return FFSPMV_ERR_ARG;
         if ((hs[j]->A.nrows > 0 && !d_y[j]) || (hs[j]->A.ncols > 0 && !d_x[j])) return FFSPMV_ERR_ARG;

@@ -9,6 +9,7 @@
 // entry point makes no cudaMalloc, cudaFree or other allocating call; the
 // scratch (the exact per-column sums) lives in `g_scratch` below, which every
 // GPU that loads the library holds until the process exits.
+#include <atomic>
 #include <cstring>
 
 #include "ff_internal.cuh"
@@ -25,7 +26,8 @@ static __device__ __align__(256) u64 g_scratch[kScratchElems];
 
 // Device address of g_scratch per device, filled on the first call made with
 // that device current (in host code the name g_scratch is only a stand-in).
-u64 *g_scratch_ptr[kMaxDevices] = {};
+// Host threads that race on the first call all store the same address.
+std::atomic<u64 *> g_scratch_ptr[kMaxDevices] = {};
 
 __global__ void k_zero(u64 *__restrict__ p, long long n)
 {
@@ -64,17 +66,16 @@ __global__ void k_finish(long long ncols, int nv, const u64 *__restrict__ acc,
     *yp = combine(red64(acc[t], M), yp, false, M);
 }
 
-ffspmv_status scratch_for_current_device(u64 **out)
+// The array of device `dev`, which must be the current device.
+ffspmv_status scratch_for_device(int dev, u64 **out)
 {
-    int dev = 0;
-    FF_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return FFSPMV_ERR_UNSUPPORTED;
-    if (!g_scratch_ptr[dev]) {
-        u64 *p = nullptr;
+    u64 *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
         FF_CUDA(cudaGetSymbolAddress((void **)&p, g_scratch));
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return FFSPMV_OK;
 }
 
@@ -100,10 +101,21 @@ extern "C" ffspmv_status spmv_apply_transpose_noalloc(ffspmv_t h, const uint32_t
     long long chunk = kScratchElems / ncols;
     if (chunk > 16) chunk = 16;
     if (chunk > nvec) chunk = nvec;
+    // the handle's arrays live on h->device; the kernels run on the current one
+    int dev = 0;
+    FF_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) return FFSPMV_ERR_ARG;
     u64 *acc = nullptr;
-    ffspmv_status st = scratch_for_current_device(&acc);
+    ffspmv_status st = scratch_for_device(dev, &acc);
     if (st != FFSPMV_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->opt.value_check && nrows > 0) {
+        // the same input check as spmv_apply_transpose (a preallocated flag word)
+        bool bad = false;
+        st = check_range(d_x, nrows, ldx, nvec, h->m, h->d_status + 1, s, &bad);
+        if (st != FFSPMV_OK) return st;
+        if (bad) return FFSPMV_ERR_RANGE;
+    }
     const Mod M = make_mod(h->m, alpha, beta);
     for (long long c0 = 0; c0 < nvec; c0 += chunk) {
         const int nv = (int)(nvec - c0 < chunk ? nvec - c0 : chunk);

@@ -522,9 +522,11 @@ struct SeqState {
     // per-launch path buffers
     void *gwork = nullptr;
     size_t gwork_bytes = 0;
-    // graph cache
+    // graph cache: the kernel arguments and the two input blocks that the
+    // captured preparation launches read
     cudaGraphExec_t exec = nullptr;
     SeqArgs key;
+    const u32 *key_X = nullptr, *key_Y = nullptr;
 };
 
 void free_sequence_state(ffspmv_handle *h)
@@ -710,12 +712,17 @@ bool same_key(const SeqArgs &a, const SeqArgs &b)
 using namespace ff;
 
 extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, const uint32_t *d_Y,
-                                             int32_t s, int64_t nsteps, uint32_t *d_S,
-                                             uint32_t *d_V_next, ffspmv_stream_t stream)
+                                             int32_t s, int64_t start_step, int64_t nsteps,
+                                             uint32_t *d_S, uint32_t *d_V_state,
+                                             ffspmv_stream_t stream)
 {
-    if (!h || s < 1 || s > 32 || nsteps < 0) return FFSPMV_ERR_ARG;
+    if (!h || s < 1 || s > 32 || nsteps < 0 || start_step < 0) return FFSPMV_ERR_ARG;
     if (h->A.nrows != h->A.ncols) return FFSPMV_ERR_ARG;
     const long long n = h->A.nrows;
+    // a resumed sequence starts from the state an earlier call left in d_V_state
+    if (start_step > 0 && !d_V_state) return FFSPMV_ERR_ARG;
+    if (start_step > 0) d_Y = d_V_state;
+    uint32_t *d_V_next = d_V_state;
     if (n > 0 && (!d_X || !d_Y)) return FFSPMV_ERR_ARG;
     if (nsteps > 0 && !d_S) return FFSPMV_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -723,7 +730,7 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
     SeqState *q = (SeqState *)h->seq_state;
     if (!q) return FFSPMV_ERR_OOM;
 
-    bool persistent = h->opt.sequence_mode == 0 && h->m <= 65536u && s <= kS && n > 0;
+    bool persistent = h->opt.sequence_mode == 0 && h->m <= 65536u && s <= kS && n > 0 && nsteps > 0;
     if (persistent && !q->layout_tried) {
         q->layout_tried = true;
         q->layout_ok = build_seq_layout(h, *q);
@@ -783,7 +790,7 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
     a.M = make_mod(h->m, 1, 0);
 
     // the graph: prepare X/Y, clear barrier + status, run the persistent kernel
-    if (!q->exec || !same_key(a, q->key)) {
+    if (!q->exec || !same_key(a, q->key) || q->key_X != d_X || q->key_Y != d_Y) {
         if (q->exec) cudaGraphExecDestroy(q->exec);
         q->exec = nullptr;
         cudaStream_t cs;
@@ -820,6 +827,8 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
             return sequence_per_launch(h, *q, d_X, d_Y, s, nsteps, d_S, d_V_next, st);
         }
         q->key = a;
+        q->key_X = d_X;
+        q->key_Y = d_Y;
     }
     FF_CUDA(cudaGraphLaunch(q->exec, st));
     int status = 0;

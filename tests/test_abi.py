@@ -46,7 +46,7 @@ def test_host_side_argument_errors_without_gpu():
     assert L.spmv_create_hybrid(None, 1, 1, 0, None, None, None, 7, None, None) == 1
     assert L.spmv_create_hybrid(ctypes.byref(h), -1, 1, 0, None, None, None, 7, None, None) == 1
     assert L.spmv_apply(None, None, 1, None, 1, 1, 1, 0, None) == 1
-    assert L.spmv_block_sequence(None, None, None, 16, 10, None, None, None) == 1
+    assert L.spmv_block_sequence(None, None, None, 16, 0, 10, None, None, None) == 1
     assert L.spmv_batch_apply(-1, None, None, None, None, None) == 1
     assert L.spmv_apply_gf2(None, 0, None, None, 1, 0, None) == 1
     assert L.spmv_check_status(None, None) == 1

@@ -45,6 +45,56 @@ def test_resume_from_checkpoint(lib, mode):
     assert np.array_equal(np.concatenate([S1, S2]), full)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_resume_with_start_step_and_state(lib, mode):
+    # the boundary's resume form: start_step > 0 continues from d_V_state,
+    # which is advanced in place; d_Y is not read
+    import torch
+    p, s = 65521, 8
+    A = gen.wiedemann_matrix(seed=16, n=3000)
+    X = gen.uniform_block(13, A.nrows, s, p)
+    Y = gen.uniform_block(14, A.nrows, s, p, key=6)
+    M = lib.Matrix.from_csr(A, sequence_mode=mode)
+    Xd = to_dev(X)
+    S1, V = M.block_sequence(Xd, to_dev(Y), 11, want_next=True)
+    S2 = M.resume_sequence(Xd, V, 11, 9)
+    S3 = M.resume_sequence(Xd, V, 20, 6)
+    torch.cuda.synchronize()
+    full, Vw = oracle.csr_block_sequence(A, X, Y, 26, want_next=True)
+    got = np.concatenate([to_host(S1), to_host(S2), to_host(S3)]).reshape(26, s, s)
+    assert np.array_equal(got, full)
+    assert np.array_equal(to_host(V).reshape(A.nrows, s), Vw)
+    with pytest.raises(lib.FFSPMVError) as e:      # start_step > 0 needs the state
+        lib.spmv_block_sequence(M.handle, Xd, to_dev(Y), s, 3, 2,
+                                torch.empty((2, s, s), dtype=torch.int32, device="cuda"), None)
+    assert e.value.status == 1
+
+
+def test_one_handle_new_blocks_each_call(lib):
+    # the captured graph of the persistent kernel reads X and Y: a later call
+    # on the same handle with other blocks (same sizes) must use them
+    import torch
+    p, s, L = 65521, 16, 15
+    A = gen.wiedemann_matrix(seed=17, n=4000)
+    M = lib.Matrix.from_csr(A)
+    blocks = [(gen.uniform_block(20 + k, A.nrows, s, p), gen.uniform_block(30 + k, A.nrows, s, p, key=k))
+              for k in range(3)]
+    S = torch.empty((L, s, s), dtype=torch.int32, device="cuda")
+    dev = [(to_dev(X), to_dev(Y)) for X, Y in blocks]   # all alive: distinct addresses
+    for k in (0, 1, 2, 0):
+        X, Y = blocks[k]
+        lib.spmv_block_sequence(M.handle, dev[k][0], dev[k][1], s, 0, L, S, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(S).reshape(L, s, s), oracle.csr_block_sequence(A, X, Y, L)), k
+    # and a resume on the same handle whose state buffer is the previous Y
+    X, Y = blocks[1]
+    S1, V = M.block_sequence(to_dev(X), to_dev(Y), 7, want_next=True)
+    S2 = M.block_sequence(to_dev(X), V, 8)
+    torch.cuda.synchronize()
+    assert np.array_equal(np.concatenate([to_host(S1), to_host(S2)]).reshape(15, s, s),
+                          oracle.csr_block_sequence(A, X, Y, 15))
+
+
 def test_general_matrix_and_large_prime(lib):
     # power-law rows do not fit the DIA + ELL_R layout; 2^31-1 needs 4 limbs:
     # both go through the per-launch path
@@ -88,8 +138,15 @@ def test_timeout_hook_returns_status_and_handle_survives(lib):
 
 
 def test_full_size_wiedemann(lib):
-    # 100k x 100k, s = 16, the benchmark's 12 502 steps; the oracle checks
-    # the first 24 steps whole and one (a, b) entry over every step.
+    # 100k x 100k, s = 16, the benchmark's 12 502 steps.  The oracle checks
+    # the first 24 steps whole, one (a, b) entry over every step, and every
+    # entry of every step through random fingerprints: for u, w uniform in
+    # (Z/pZ)^s, u^T S_i w = (X u)^T A^i (Y w) mod p is the scalar sequence of
+    # the projected blocks X u and Y w, which the oracle computes with one
+    # column each.  A wrong block E != 0 has u^T E w = 0 with probability at
+    # most 2/p for one (u, w) (a nonzero bilinear form of degree 2), so two
+    # fingerprints miss a wrong S_i with probability below 1e-9.
+    from concurrent.futures import ThreadPoolExecutor
     p, s = 65521, 16
     A = gen.wiedemann_matrix(seed=1003)
     n = A.nrows
@@ -98,7 +155,22 @@ def test_full_size_wiedemann(lib):
     Y = gen.uniform_block(1003, n, s, p, key=1)
     S = run(lib, A, X, Y, L)
     assert S.shape == (L, s, s)
-    assert np.array_equal(S[:24], oracle.csr_block_sequence(A, X, Y, 24))
+    rng = np.random.default_rng(77)
+    fps = [(rng.integers(0, p, s, dtype=np.uint64), rng.integers(0, p, s, dtype=np.uint64))
+           for _ in range(2)]
     a, b = 5, 11
-    col = oracle.csr_block_sequence(A, X[:, a:a + 1], Y[:, b:b + 1], L).reshape(L)
-    assert np.array_equal(S[:, a, b], col)
+    jobs = [(X, Y, 24), (X[:, a:a + 1], Y[:, b:b + 1], L)]
+    for u, w in fps:
+        # inputs below 2^16, so these u64 sums of 16 products are exact
+        xu = ((X.astype(np.uint64) @ u) % p).astype(np.uint32).reshape(n, 1)
+        yw = ((Y.astype(np.uint64) @ w) % p).astype(np.uint32).reshape(n, 1)
+        jobs.append((xu, yw, L))
+    with ThreadPoolExecutor(len(jobs)) as ex:       # the oracle releases the GIL
+        res = list(ex.map(lambda j: oracle.csr_block_sequence(A, *j), jobs))
+    assert np.array_equal(S[:24], res[0])
+    assert np.array_equal(S[:, a, b], res[1].reshape(L))
+    S64 = S.astype(np.uint64)
+    for (u, w), want in zip(fps, res[2:]):
+        # u^T S_i w: terms below 2^48, 256 of them, exact in u64
+        got = ((S64 * u[None, :, None]) % p * w[None, None, :]).sum(axis=(1, 2)) % p
+        assert np.array_equal(got.astype(np.uint32), want.reshape(L))

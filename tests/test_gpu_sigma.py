@@ -150,6 +150,19 @@ def test_wiedemann_100k_generator(lib):
     Fh = F.cpu().numpy().view(np.uint32).astype(np.int64)
     for k in (0, 1, 2, 777, L // 2, L - 2, L - 1):   # P F = 0 mod x^L, sampled
         assert not np.any(_coeff_np(P, Fh, k, e) % p), k
+    # every order through random fingerprints: u^T (P F)_k w = 0 for all k < L,
+    # the coefficients of sum_j (u^T P)_j (F w)_j; a nonzero coefficient block
+    # passes one fingerprint with probability at most 2/p
+    for seed in (1, 2):
+        fr = np.random.default_rng(seed)
+        u = fr.integers(0, p, 2 * s, dtype=np.int64)
+        w = fr.integers(0, p, s, dtype=np.int64)
+        uP = np.einsum("i,kij->kj", u, P) % p       # (e+1) x 2s, sums below 2^42
+        Fw = np.einsum("kjl,l->kj", Fh, w) % p      # L x 2s
+        r = np.zeros(L, dtype=np.int64)
+        for j in range(2 * s):                      # sums below 2^46 per j
+            r = (r + np.convolve(uP[:, j], Fw[:, j])[:L]) % p
+        assert not np.any(r), int(np.flatnonzero(r)[0])
     rows = sorted(range(2 * s), key=lambda i: (delta[i], i))[:s]
     assert sum(delta[i] for i in rows) == N
     lead = np.stack([P[delta[i], i, :s] for i in rows])

@@ -294,3 +294,16 @@ def test_generators_shapes():
     for i in range(W.nrows):
         c = W.col[W.row_ptr[i]:W.row_ptr[i + 1]]
         assert np.all(np.diff(c) > 0)
+
+
+def test_threaded_oracle_equals_single_thread():
+    # the all-core timing form splits rows over threads; its results are the
+    # single-thread definition's, for both products, alpha/beta and blocks
+    A = gen.powerlaw_matrix(seed=5, n=3000, lmax=300, m=2**31 - 1, pm_fraction=0.3)
+    x = gen.uniform_block(3, A.ncols, 3, A.modulus).reshape(-1, 3)
+    y0 = gen.uniform_block(4, A.nrows, 3, A.modulus).reshape(-1, 3)
+    for t in (2, 5, 16):
+        assert np.array_equal(oracle.csr_spmv(A, x, y=y0, alpha=5, beta=7, threads=t),
+                              oracle.csr_spmv(A, x, y=y0, alpha=5, beta=7))
+        assert np.array_equal(oracle.csr_spmv_transpose(A, x, y=y0, alpha=5, beta=7, threads=t),
+                              oracle.csr_spmv_transpose(A, x, y=y0, alpha=5, beta=7))
