@@ -326,6 +326,31 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
     return out
 
 
+def extra_multivec(torch, ff, flush, stream):
+    """Y = A X on the 1M power-law matrix (m = 65521) for blocks of 1 to 16
+    vectors through AUTO: one vector runs the x-panel kernel; from three
+    vectors on, a binned plan reads the matrix once for the whole block
+    (Sec. 2.5.1), next to the time of that many single-vector products."""
+    sp = stream.cuda_stream
+    m = 65521
+    A = gen.powerlaw_matrix(seed=SEED, m=m)
+    M = ff.Matrix.from_csr(A, transpose_mode=ff.TRANSPOSE.NONE)
+    res = {"workload": f"powerlaw 1M x 1M ({A.nnz} nnz), m={m}, AUTO, L2 flushed"}
+    single = None
+    for nv in (1, 2, 4, 8, 16):
+        x = torch.from_numpy(gen.uniform_block(SEED, A.ncols, nv, m).view(np.int32)).cuda()
+        y = torch.empty((A.nrows, nv), dtype=torch.int32, device="cuda")
+        fn = lambda: ff.spmv_apply(M.handle, x, nv, y, nv, nv, 1, 0, sp)
+        for _ in range(3):
+            fn()
+        ms = statistics.median(timed_steps(torch, fn, 10, flush, stream))
+        single = ms if nv == 1 else single
+        res[f"nvec={nv}"] = {"ms": round(ms, 4), "gnnz_vec_s": round(A.nnz * nv / ms / 1e6, 1),
+                             "launches": M.launches(False, nv),
+                             "vs_nvec_single_products": round(nv * single / ms, 2)}
+    return res
+
+
 def extra_sequence(torch, ff, stream):
     sp = stream.cuda_stream
     p, s = 65521, 16
@@ -613,7 +638,8 @@ def main():
     wanted = [e for e in args.extras.split(",") if e]
     del M
     torch.cuda.empty_cache()
-    for name, fn in (("polymat", lambda: extra_polymat(torch, ff, stream)),
+    for name, fn in (("multivec", lambda: extra_multivec(torch, ff, flush, stream)),
+                     ("polymat", lambda: extra_polymat(torch, ff, stream)),
                      ("gf2", lambda: extra_gf2(torch, ff, flush, stream)),
                      ("formats", lambda: extra_formats(torch, ff, flush, stream)),
                      ("sequence", lambda: extra_sequence(torch, ff, stream)),

@@ -92,6 +92,8 @@ typedef struct {
                                   bit 1 = the x-panel kernel never issues the copies of the second
                                   stage of each CTA, so the waits for it run out (the status word
                                   read by spmv_check_status) */
+    int32_t panel_cluster;     /* x-panel layout: CTAs per cluster (column groups); 0 = chosen by
+                                  the builder, 1, 2 or 4 to force one */
 } ffspmv_options;
 
 /* Fill *opt with the defaults. */
@@ -119,7 +121,12 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
  * Y <- alpha*A*X + beta*Y (mod m), Sec. 2 (the operation y <- alpha A x +
  * beta y and its block form).  d_x: ncols x nvec (ldx), d_y: nrows x nvec
  * (ldy); 1 <= nvec; alpha, beta < m (reduced if not).  beta = 0 never reads
- * d_y ("apply": y <- A x).  d_x and d_y must not overlap.
+ * d_y ("apply": y <- A x).  d_x and d_y must not overlap.  On a handle whose
+ * plan is the x-panel layout, a block of 3 or more vectors runs a binned plan
+ * that reads the matrix once for the whole block (Sec. 2.5.1); the first
+ * such call builds that plan (synchronous, allocates once per handle and
+ * direction).  Calls on one handle must not overlap on the GPU (the x-panel
+ * plan stages x in a buffer of the handle).
  */
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx,
                          uint32_t *d_y, int64_t ldy, int32_t nvec,
@@ -218,7 +225,9 @@ const char *ffspmv_last_error(void);
 ffspmv_status spmv_describe_plan(ffspmv_t h, char *buf, size_t len);
 
 /* Number of kernel launches that one spmv_apply (transpose = 0) or
- * spmv_apply_transpose (transpose = 1) call with nvec vectors enqueues. */
+ * spmv_apply_transpose (transpose = 1) call with nvec vectors enqueues
+ * (for a wide block on an x-panel handle this builds the binned plan that
+ * the call would use, as spmv_apply does). */
 ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec,
                                   int64_t *launches);
 
@@ -253,6 +262,30 @@ ffspmv_status spmv_apply_gf2(ffspmv_t h, int32_t transpose, const uint64_t *d_X,
  * apply calls are asynchronous and do not read the word themselves.
  */
 ffspmv_status spmv_check_status(ffspmv_t h, ffspmv_stream_t stream);
+
+/*
+ * Testing aid for the x-panel layout (FFSPMV_FMT_PANEL); the paper has no
+ * counterpart.  Runs only the host half of the layout for the CSR matrix
+ * (row_ptr, col, values as in spmv_create_hybrid, host memory) with q CTAs
+ * per cluster (1, 2 or 4) and `clusters` resident clusters, then decodes
+ * every stored entry back to (row, column, value) and writes the first `cap`
+ * of them to out_row / out_col / out_val (host arrays); *out_n = the number
+ * decoded.  Padding (value 0) is skipped, so are explicit zeros; rows longer
+ * than 32768 entries are not part of the layout.  use_pm1 = 1 puts the +-1
+ * entries in value-free sections (decoded as 1 or m - 1).  stats (NULL or
+ * double[10]): stages, share of lanes that are packs, mean shared-memory
+ * wavefronts of a warp's x gather and of its row-sum atomic per slot (the
+ * bank model of the layout), entries in +-1 sections, padding entries, panel
+ * bytes, stage capacity, packs that break the kernel's segmented warp sum
+ * (entries not all of one row, or lanes of one row and section that are not
+ * contiguous within their warp; 0 when the layout is sound), q.  No device
+ * call is made.
+ */
+ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const int64_t *row_ptr,
+                                  const int32_t *col, const uint32_t *values, uint32_t m,
+                                  int32_t use_pm1, int32_t q, int32_t clusters, int64_t cap,
+                                  int64_t *out_row, int64_t *out_col, uint32_t *out_val,
+                                  int64_t *out_n, double *stats);
 
 #ifdef __cplusplus
 }

@@ -39,6 +39,7 @@ class Options(ctypes.Structure):
         ("guard_bytes", ctypes.c_int64),
         ("sequence_mode", ctypes.c_int32),
         ("test_hooks", ctypes.c_int32),
+        ("panel_cluster", ctypes.c_int32),
     ]
 
 
@@ -78,6 +79,9 @@ def _declare(L):
     L.spmv_apply_transpose_noalloc.restype = ctypes.c_int
     L.spmv_count_launches.argtypes = [_P, _I32, _I32, ctypes.POINTER(_I64)]
     L.spmv_count_launches.restype = ctypes.c_int
+    L.ffspmv_panel_decode.argtypes = [_I64, _I64, _P, _P, _P, _U32, _I32, _I32, _I32, _I64, _P, _P, _P,
+                                      ctypes.POINTER(_I64), _P]
+    L.ffspmv_panel_decode.restype = ctypes.c_int
     L.spmv_check_status.argtypes = [_P, _P]
     L.spmv_check_status.restype = ctypes.c_int
     L.spmv_apply_gf2.argtypes = [_P, _I32, _P, _P, _I32, _I32, _P]

@@ -45,6 +45,11 @@ void destroy_handle(ffspmv_handle *h)
     if (!h) return;
     free_plan(h->A);
     free_plan(h->AT);
+    for (ff::Plan *&mp : h->multi) {
+        if (mp) free_plan(*mp);
+        delete mp;
+        mp = nullptr;
+    }
     if (h->scatter) cudaFree(h->scatter);
     if (h->csr_arena) cudaFree(h->csr_arena);
     if (h->d_status) cudaFree(h->d_status);
@@ -175,6 +180,7 @@ void ffspmv_options_default(ffspmv_options *o)
     o->guard_bytes = 0;
     o->sequence_mode = 0;
     o->test_hooks = 0;
+    o->panel_cluster = 0;
 }
 
 const char *ffspmv_status_string(ffspmv_status s)
@@ -279,6 +285,39 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
     return FFSPMV_OK;
 }
 
+// The binned plan of A (or A^T) for wide blocks on an x-panel handle, built
+// on first use from the handle's host copy of the matrix (synchronous).
+static ffspmv_status ensure_multi(ffspmv_t h, bool transpose, const Plan **out)
+{
+    Plan *&mp = h->multi[transpose ? 1 : 0];
+    if (!mp) {
+        Plan *np = new (std::nothrow) Plan();
+        if (!np) return FFSPMV_ERR_OOM;
+        ffspmv_options o = h->opt;
+        o.priority_format = FFSPMV_FMT_BINNED;
+        o.selector = FFSPMV_SEL_HEURISTIC;
+        const long long nr = h->A.nrows, nc = h->A.ncols;
+        ffspmv_status st;
+        if (!transpose) {
+            st = build_plan_ex(*np, nr, nc, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), h->m, o, nullptr);
+        } else {
+            std::vector<long long> tptr;
+            std::vector<int> tcol;
+            std::vector<u32> tval;
+            transpose_csr(nr, nc, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), tptr, tcol, tval);
+            st = build_plan_ex(*np, nc, nr, tptr.data(), tcol.data(), tval.data(), h->m, o, nullptr);
+        }
+        if (st != FFSPMV_OK) {
+            free_plan(*np);
+            delete np;
+            return st;
+        }
+        mp = np;
+    }
+    *out = mp;
+    return FFSPMV_OK;
+}
+
 static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_x,
                                   int64_t ldx, uint32_t *d_y, int64_t ldy,
                                   int32_t nvec, uint32_t alpha, uint32_t beta,
@@ -299,11 +338,15 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     if (out_rows == 0) return FFSPMV_OK;
     if (transpose && h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC)
         return run_scatter_transpose(h, d_x, ldx, d_y, ldy, nvec, alpha % h->m, beta % h->m, st);
-    const Plan &P = transpose ? h->AT : h->A;
+    const Plan *P = transpose ? &h->AT : &h->A;
+    if (P->panel.on && nvec >= kPanelMultiMin) {
+        ffspmv_status s = ensure_multi(h, transpose, &P);
+        if (s != FFSPMV_OK) return s;
+    }
     PanelCtl ctl;
     ctl.status = h->d_status + 2;
     ctl.skip_stage = (h->opt.test_hooks & 2) ? 1 : -1;
-    return run_plan(P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, &ctl);
+    return run_plan(*P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, &ctl);
 }
 
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx, uint32_t *d_y,
@@ -382,7 +425,15 @@ ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec, i
         const int chunk = nvec < 16 ? nvec : 16;
         n += 2LL * ((nvec + chunk - 1) / chunk);
     } else {
-        n += count_plan_launches(transpose ? h->AT : h->A, nvec);
+        const Plan &P = transpose ? h->AT : h->A;
+        if (P.panel.on && nvec >= kPanelMultiMin) {
+            const Plan *mp = nullptr;
+            ffspmv_status s = ensure_multi(h, transpose != 0, &mp);
+            if (s != FFSPMV_OK) return s;
+            n += count_plan_launches(*mp, nvec);
+        } else {
+            n += count_plan_launches(P, nvec);
+        }
     }
     *launches = n;
     return FFSPMV_OK;

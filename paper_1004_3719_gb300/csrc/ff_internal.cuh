@@ -179,29 +179,61 @@ struct Phase {
 // shared memory, and kPanelStages x slots hold the panels they use (a panel
 // is copied once, with its first stage).  One warp of the CTA issues the bulk
 // copies of each stage once the buffer's previous stage is done with; the
-// other warps wait for the copies and sum.  An entry word
-// packs (row in group << kPanelColBits | byte offset of its x in the panel);
-// rows ascend within a stage.  Row sums stay in shared memory (u32 sums of
-// terms below 2m when m <= 2^16 -- at most kPanelLong of them, so below 2^32 --
-// u64 sums of terms below m otherwise); the q CTAs of a cluster add their
-// partial sums through distributed shared memory.
+// other warps wait for the copies and sum.
+//
+// Every CTA first converts its share of x into the staged copy (u16 or u32,
+// contiguous) and meets the others at a grid barrier before the first panel
+// is copied in; the launch is one CTA per SM, all resident.
+//
+// A stage is a list of lanes of eight entries each, in four sections:
+// general packs, general singles, +-1 packs, +-1 singles.  A pack holds eight
+// entries of one row: the lane sums them and the lanes of one warp that
+// carry the same row add their sums together (a segmented warp sum) before
+// one shared-memory atomic.  Single lanes add each of their eight terms.  The
+// host orders the entries of every 32 lanes so that, slot by slot, the x
+// words and the row sums a warp touches fall in distinct shared-memory banks
+// as far as it can.  The +-1 sections carry no values (Sec. 2.4.2): bit 15
+// of the entry word gives the sign.  In memory the eight entries of lane j
+// of a 32-lane block of c lanes sit at 4j..4j+3 and 4c+4j..4c+4j+3 of the
+// block (each 16-byte load of a warp reads 512 contiguous bytes); values
+// (general lanes only) are lane by lane for u16, interleaved the same way
+// for u32.  Entry word: (row in group << 16) | (sign << 15) | x element of
+// the panel.  Row sums stay in shared memory (u32 sums of terms below 2m when
+// m <= 2^16 -- at most kPanelLong of them, so below 2^32 -- u64 sums of terms
+// below 2^32 otherwise); the q CTAs of a cluster add their partial sums
+// through distributed shared memory.
 constexpr int kPanelConsumers = 512;          // 16 warps sum entries
-constexpr int kPanelThreads = kPanelConsumers + 32;  // + one warp issuing the copies
-constexpr int kPanelPerThread = 8;            // entries a thread takes per step
 constexpr int kPanelStages = 3;
-constexpr int kPanelBarBytes = 64;            // full and empty mbarrier of each stage buffer
-constexpr int kPanelDescBytes = 64;           // (entries, x slot) of the stage in each buffer
+constexpr int kPanelThreads = kPanelConsumers + 32 * kPanelStages;  // + one copy warp per stage buffer
+constexpr int kPanelPerThread = 8;            // entries a lane takes per step
+constexpr int kPanelBarBytes = 128;           // full and empty mbarrier of each stage buffer
+constexpr int kPanelDescBytes = 128;          // (entries, general, packs, x slot) of each buffer
+constexpr u32 kPanelSlotMask = 7u;            // PanelStage::xs: x slot
+constexpr u32 kPanelNewX = 8u;                // PanelStage::xs: the panel is copied in with this stage
+static_assert(16 * kPanelStages <= kPanelBarBytes && kPanelStages <= 8, "mbarriers and slots of the stage buffers");
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
-constexpr int kPanelAhead = 4;                // stages of entries pulled into L2 ahead of use
-constexpr int kPanelColBits = 16;             // byte offset of the column in its x panel
+constexpr unsigned kPanelGridSpin = 1u << 20; // polls of the grid barrier before giving up
+constexpr int kPanelAhead = 2;                // rounds of a buffer's stages pulled into L2 ahead of use
+constexpr u32 kPanelIdxMask = 0x7fffu;        // x element of the panel
+constexpr u32 kPanelNeg = 0x8000u;            // a -1 entry (+-1 sections)
 constexpr long long kPanelLong = 32768;       // longer rows go to split CSR segments
 constexpr int kPanelSmemMax = 227 * 1024;
+constexpr int kPanelMaxPe = 32760;            // stage entries (fits the 16-bit pack counts)
+// Blocks of this many vectors or more skip the x-panel plan: a binned plan
+// reads the matrix once for all of them (Sec. 2.5.1), where the panel kernel
+// takes one pass per vector.
+constexpr int kPanelMultiMin = 3;
+static_assert(16 * kPanelStages + 4 <= kPanelDescBytes, "stage descriptors and the grid generation word");
 
 struct PanelStage {
-    u32 xoff;  // first staged-x element of the panel (a multiple of 8)
+    u32 xoff;  // first staged-x element of the panel (16-byte aligned)
     u32 k0;    // first entry (a multiple of 8)
+    u32 v0;    // first value (a multiple of 8): values of the general lanes only
     u32 nent;  // entries, a multiple of 8, at most pe
-    u32 xs;    // x slot (bits 0-1); bit 2 set: the panel is copied in with this stage
+    u32 ngen;  // entries of the general sections (a multiple of 8), first in the stage
+    u32 npg;   // entries of the general packs, first in the general sections
+    u32 npp;   // entries of the +-1 packs, first in the +-1 sections
+    u32 xs;    // x slot (kPanelSlotMask); kPanelNewX set: the panel is copied in with this stage
 };
 
 struct PanelPart {
@@ -211,10 +243,13 @@ struct PanelPart {
     int ngroup = 0;      // row groups
     int rows_max = 0;    // most rows in one group
     int resident = 0;    // clusters of q resident at once
-    int px = 0;          // bytes of x per panel (a multiple of 16)
+    int px = 0;          // bytes of x per panel (a multiple of 128)
     int pe = 0;          // entry capacity of a stage (a multiple of 8)
-    int eb = 0;          // bytes per stage's entry buffer (a multiple of 16)
+    int eb = 0;          // bytes per stage's entry buffer (a multiple of 128)
+    long long ncols = 0; // x elements to stage
     long long nstage = 0;
+    long long npm = 0;   // entries in the +-1 sections
+    long long npad = 0;  // zero entries padding the general sections
     size_t smem = 0;     // dynamic shared memory per CTA
     const u32 *grp_row0 = nullptr;    // [ngroup + 1]
     const u32 *stage_ptr = nullptr;   // [ngroup * q + 1]
@@ -222,6 +257,7 @@ struct PanelPart {
     const u32 *ent = nullptr;
     const void *val = nullptr;
     void *xh = nullptr;  // contiguous u16 / u32 copy of one x column, zero padded
+    u32 *gbar = nullptr; // grid barrier: arrivals, generation
 };
 
 // Most clusters of q CTAs of the panel kernel resident at once with `smem`
@@ -274,6 +310,9 @@ struct ffspmv_handle {
     int *d_status = nullptr;   // device status word (timeouts)
     // patterns of the odd entries of A and A^T for the GF(2) products
     ff::Gf2Pattern *gf2[2] = {nullptr, nullptr};
+    // binned plans of A and A^T for blocks of kPanelMultiMin or more vectors
+    // when the plan is the x-panel layout (built on first use)
+    ff::Plan *multi[2] = {nullptr, nullptr};
 };
 
 namespace ff {

@@ -1,6 +1,7 @@
 // Plan-building entry points shared between the host translation units.
 #pragma once
 
+#include <functional>
 #include <vector>
 
 #include "ff_internal.cuh"
@@ -38,6 +39,28 @@ ffspmv_status build_rows_plan(Plan &P, const PlanSource &src, const std::vector<
 constexpr int kFormats = 10;
 BinChoice format_choice(int f, int pm);
 bool format_valid(int f, int bin, long long maxlen);
+
+// Host half of the x-panel layout (panel.cu): geometry, stage descriptors,
+// entry words and values (u32 here; stored as u16 when m <= 2^16).
+struct PanelHost {
+    bool small = true;
+    int q = 1, ngroup = 0, rows_max = 0, resident = 0, px = 0, pe = 0, eb = 0;
+    size_t smem = 0;
+    long long pcols = 0, nstage = 0, npm = 0, npad = 0;
+    std::vector<u32> grp_row0, stage_ptr;
+    std::vector<PanelStage> stage;
+    std::vector<u32> ent, val;
+};
+
+// Rows longer than kPanelLong are left out (the caller adds split CSR
+// segments for them).  pm_on: +-1 entries (cls != 0) go to value-free
+// sections.  force_q: 1, 2 or 4 forces the cluster size, else the builder
+// picks it; max_clusters(q, small) gives the clusters of q CTAs resident at
+// once.  False when the matrix has nothing to stage or exceeds the layout's
+// limits.
+bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *col, const u32 *val,
+                  const unsigned char *cls, u32 m, bool pm_on, int force_q,
+                  const std::function<int(int, bool)> &max_clusters, PanelHost &H);
 
 void transpose_csr(long long nrows, long long ncols, const long long *ptr,
                    const int *col, const u32 *val, std::vector<long long> &tptr,

@@ -513,18 +513,13 @@ static PlanParams params_of(const Phase &ph, int acc_wide)
 }
 
 // ---------------------------------------------------------------------------
-// x-panel layout (the layout is described with PanelPart).  x is first copied
-// into a contiguous u16 / u32 array; the panel kernel then streams stages of
-// entries and values, and the x panels they use, into shared memory with
-// cp.async, kPanelStages stages in flight, and adds each term into its row's
-// shared-memory sum.  The terms
-// of a warp that all fall on one row are summed in registers and added once.
+// x-panel layout (PanelPart, ff_internal.cuh; the host half is panel.cu).
+// Contiguous u16 / u32 copy of one x column, for plans whose CTAs are not all
+// resident at once (their panel kernel cannot stage x itself).
 template <typename XT>
 __global__ void __launch_bounds__(256) k_x_stage(const u32 *__restrict__ x, long long ldx, long long n,
                                                  XT *__restrict__ xs)
 {
-    // the panel kernel may start now; it waits for this grid before reading xs
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const long long nth = (long long)gridDim.x * blockDim.x;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long done = 0;
@@ -547,14 +542,23 @@ __global__ void __launch_bounds__(256) k_x_stage(const u32 *__restrict__ x, long
     for (long long i = done + t; i < n; i += nth) xs[i] = (XT)x[i * ldx];
 }
 
-__device__ __forceinline__ void panel_cp16(u32 dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 16 bytes at the same shared-memory offset in CTA `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ uint4 ld_cluster_v4(const T *local, u32 rank)
+{
+    u32 a = (u32)__cvta_generic_to_shared(local), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(r)
+                 : "memory");
+    return v;
 }
 
 template <typename T>
@@ -582,6 +586,12 @@ __device__ __forceinline__ u32 red32_lazy(u32 t, u32 m, u32 mu) { return t - __u
 __device__ __forceinline__ void mbar_init(u32 bar, u32 count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Raise the bytes the current phase of `bar` waits for, without arriving.
+__device__ __forceinline__ void mbar_add_tx(u32 bar, u32 bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes)
@@ -626,20 +636,45 @@ __device__ __forceinline__ void mbar_arrive(u32 bar)
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ u32 ld_acquire_gpu(const u32 *p)
+{
+    u32 v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ u32 atom_add_release_gpu(u32 *p, u32 v)
+{
+    u32 old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_release_gpu(u32 *p, u32 v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Orders this thread's generic-proxy accesses of global memory with later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 template <bool SMALL>
 __global__ void __launch_bounds__(kPanelThreads, 1)
-k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int *status, int skip_stage)
+k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__restrict__ y, long long ldy,
+        const Mod M, int *status, int skip_stage, int fused)
 {
     typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
     constexpr int VB = SMALL ? 2 : 4;
     constexpr int kWarps = kPanelConsumers / 32;
-    extern __shared__ __align__(16) unsigned char panel_smem[];
+    extern __shared__ __align__(128) unsigned char panel_smem[];
     const int PX = P.px, EB = P.eb;
     // [x slots][entry buffers][full mbarriers][empty mbarriers][stage descriptors][row sums]
     unsigned char *ebuf = panel_smem + kPanelStages * PX;
     unsigned char *bars = ebuf + kPanelStages * EB;
-    uint2 *desc = reinterpret_cast<uint2 *>(bars + kPanelBarBytes);  // (entries, x slot) per buffer
+    uint4 *desc = reinterpret_cast<uint4 *>(bars + kPanelBarBytes);  // (entries, general, packs, x slot)
+    u32 &s_gen = *reinterpret_cast<u32 *>(bars + kPanelBarBytes + 16 * kPanelStages);  // grid barrier generation
     AT *acc = reinterpret_cast<AT *>(bars + kPanelBarBytes + kPanelDescBytes);
     const int q = P.q;
     const int cta = blockIdx.x, g = cta / q, rank = cta % q;
@@ -649,124 +684,235 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
     const u32 full0 = (u32)__cvta_generic_to_shared(bars), empty0 = full0 + 8u * kPanelStages;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
+    if (fused) {
+        // this CTA's share of x, converted into the staged copy that every
+        // CTA's bulk copies read
+        const long long G = gridDim.x;
+        const long long share = ((P.ncols + G - 1) / G + 7) / 8 * 8;
+        const long long lo = min(P.ncols, (long long)cta * share), hi = min(P.ncols, lo + share);
+        XT *xh = reinterpret_cast<XT *>(P.xh);
+        long long done = lo;
+        if (ldx == 1 && ((uintptr_t)x & 15u) == 0) {
+            // four 16-byte loads in flight per thread before their stores
+            const long long i1 = hi / 4;
+            for (long long i0 = lo / 4 + t; i0 < i1; i0 += 4 * kPanelThreads) {
+                uint4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * kPanelThreads < i1) v[u] = __ldg(reinterpret_cast<const uint4 *>(x) + i0 + u * kPanelThreads);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long i = i0 + u * kPanelThreads;
+                    if (i >= i1) break;
+                    if constexpr (SMALL) {
+                        uint2 o;
+                        o.x = (v[u].x & 0xffffu) | (v[u].y << 16);
+                        o.y = (v[u].z & 0xffffu) | (v[u].w << 16);
+                        reinterpret_cast<uint2 *>(xh)[i] = o;
+                    } else {
+                        reinterpret_cast<uint4 *>(xh)[i] = v[u];
+                    }
+                }
+            }
+            done = max(lo, hi / 4 * 4);
+        }
+        for (long long i = done + t; i < hi; i += kPanelThreads) xh[i] = (XT)__ldg(x + i * ldx);
+        fence_proxy_async_global();
+    }
     for (u32 r = t; r < nr; r += kPanelThreads) acc[r] = 0;
+    __syncthreads();
     if (t == 0) {
         for (int b = 0; b < kPanelStages; ++b) {
             mbar_init(full0 + 8u * b, 1);
             mbar_init(empty0 + 8u * b, kWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::: "memory");
+        if (fused) {
+            // grid barrier: arrivals in gbar[0], generation in gbar[1]; the
+            // last CTA to arrive resets the count and moves the generation on
+            const u32 g0 = ld_acquire_gpu(P.gbar + 1);
+            s_gen = g0;
+            __threadfence();
+            if (atom_add_release_gpu(P.gbar, 1u) == gridDim.x - 1) {
+                atomicExch(P.gbar, 0u);
+                st_release_gpu(P.gbar + 1, g0 + 1);
+            }
+        }
     }
     __syncthreads();
     bool timed_out = false;
-    if (warp == kWarps) {
-        // the copying warp: descriptors 32 at a time, one per lane; lane 0
-        // waits for a buffer to be done with and issues its stage's copies
+    if (warp >= kWarps) {
+        // Copy warps.  Warp kWarps + b fills stage buffer b: stages b,
+        // b + kPanelStages, ...  A thread's bulk copies complete one after
+        // another, so each stage's copies come from two threads: lane 1 copies
+        // the entries and values (they do not depend on x, so the first one
+        // starts before the grid barrier) after adding their bytes to the
+        // stage's full barrier; lane 0, once x is staged, publishes the stage
+        // descriptor, arrives with the x panel's bytes and copies the panel.
+        const u32 b = (u32)(warp - kWarps);
+        const u32 bar = full0 + 8u * b, ebar = empty0 + 8u * b;
+        const u32 d = sbase + kPanelStages * PX + b * EB;
         const unsigned char *xh = reinterpret_cast<const unsigned char *>(P.xh);
         const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
         const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
-        // the CTA's entries are one range, stage after stage; it is pulled into
-        // L2 kPanelAhead stage capacities ahead of the copies into shared memory
-        u32 kpf = 0, kend = 0;
-        const u32 ahead = (u32)kPanelAhead * (u32)P.pe;
-        auto prefetch_to = [&](u32 want) {
-            want = min(want, kend);
-            while (kpf < want) {
-                const u32 n = min(want - kpf, 8192u);  // entries per prefetch
-                bulk_prefetch_l2(ev + (size_t)kpf * 4, n * 4u);
-                bulk_prefetch_l2(vv + (size_t)kpf * VB, n * (u32)VB);
-                kpf += n;
+        bool xready = !fused;
+        // lane 2 pulls the entries and values of this buffer's later stages
+        // into L2 (HBM latency is long; the stage buffers hold little of it)
+        auto prefetch = [&](u32 s) {
+            if (s < ns) {
+                const PanelStage a = P.stage[s0 + s];
+                bulk_prefetch_l2(ev + (size_t)a.k0 * 4, a.nent * 4u);
+                if (a.ngen) bulk_prefetch_l2(vv + (size_t)a.v0 * VB, a.ngen * (u32)VB);
             }
         };
-        if (lane == 0 && ns > 0) {
-            const PanelStage first = P.stage[s0], last = P.stage[s0 + ns - 1];
-            kpf = first.k0;
-            kend = last.k0 + last.nent;
-            prefetch_to(first.k0 + ahead);
-            // staged x is written by the launch before this one
-            asm volatile("griddepcontrol.wait;" ::: "memory");
-        }
-        for (u32 base = 0; base < ns; base += 32) {
-            PanelStage mine = {0, 0, 0, 0};
-            if (base + lane < ns) mine = P.stage[s0 + base + lane];
-            const u32 cnt = min(32u, ns - base);
-            for (u32 i = 0; i < cnt; ++i) {
-                const u32 xoff = __shfl_sync(0xffffffffu, mine.xoff, i);
-                const u32 k0 = __shfl_sync(0xffffffffu, mine.k0, i);
-                const u32 nent = __shfl_sync(0xffffffffu, mine.nent, i);
-                const u32 xs = __shfl_sync(0xffffffffu, mine.xs, i);
+        if (lane == 2)
+            for (u32 k = 1; k <= (u32)kPanelAhead; ++k) prefetch(b + k * kPanelStages);
+        for (u32 s = b; s < ns; s += kPanelStages) {
+            const PanelStage a = P.stage[s0 + s];
+            if (s >= kPanelStages) {
+                // stage s - kPanelStages of this buffer must be done with
+                u32 ok = 1;
                 if (lane == 0) {
-                    const u32 s = base + i, b = s % kPanelStages;
-                    // stage s - kPanelStages (same buffer) must be done with
-                    if (s >= kPanelStages) {
-                        const u32 eb = empty0 + 8u * b, ep = (s / kPanelStages - 1) & 1u;
-                        if (!(timed_out ? mbar_wait<1>(eb, ep) : mbar_wait(eb, ep))) timed_out = true;
-                    }
-                    if ((int)s == skip_stage) continue;  // testing: this stage is never issued
-                    const u32 bar = full0 + 8u * b;
-                    const bool newx = (xs & 4u) != 0;
-                    desc[b] = make_uint2(nent, xs & 3u);  // published by the arrive below
-                    mbar_expect_tx(bar, (newx ? (u32)PX : 0u) + nent * (4u + VB));
-                    if (newx) bulk_g2s(sbase + (xs & 3u) * PX, xh + (size_t)xoff * sizeof(XT), (u32)PX, bar);
-                    const u32 d = sbase + kPanelStages * PX + b * EB;
-                    bulk_g2s(d, ev + (size_t)k0 * 4, nent * 4u, bar);
-                    bulk_g2s(d + 4u * P.pe, vv + (size_t)k0 * VB, nent * (u32)VB, bar);
-                    prefetch_to(k0 + nent + ahead);
+                    const u32 ep = (s / kPanelStages - 1) & 1u;
+                    ok = (timed_out ? mbar_wait<1>(ebar, ep) : mbar_wait(ebar, ep)) ? 1u : 0u;
                 }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) timed_out = true;
             }
+            if ((int)s == skip_stage) continue;  // testing: this stage is never issued
+            const u32 dbytes = a.nent * 4u + a.ngen * (u32)VB;
+            if (lane == 1) mbar_add_tx(bar, dbytes);
+            __syncwarp();  // the bytes are added before lane 0's arrive
+            if (lane == 1) {
+                bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
+                if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, a.ngen * (u32)VB, bar);
+            }
+            if (lane == 2) prefetch(s + (kPanelAhead + 1) * kPanelStages);
+            if (lane == 0) {
+                if (!xready) {
+                    // every CTA's share of x is staged before the first panel copy
+                    unsigned spin = 0;
+                    while (ld_acquire_gpu(P.gbar + 1) == s_gen)
+                        if (++spin >= kPanelGridSpin) {
+                            timed_out = true;
+                            break;
+                        }
+                    fence_proxy_async_global();
+                    xready = true;
+                }
+                const bool newx = (a.xs & kPanelNewX) != 0;
+                desc[b] = make_uint4(a.nent, a.ngen, a.npg | (a.npp << 16), a.xs & kPanelSlotMask);  // published by the arrive
+                mbar_expect_tx(bar, newx ? (u32)PX : 0u);
+                if (newx) bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX, xh + (size_t)a.xoff * sizeof(XT), (u32)PX, bar);
+            }
+            __syncwarp();
         }
     } else {
         const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
+        const u32 rot = ((u32)P.pe / 8u + 31u) / 32u;  // blocks of a full stage
         for (u32 s = 0; s < ns; ++s) {
             const u32 b = s % kPanelStages;
             // after one wait has run out, the others poll once: a CTA whose
             // copies stopped coming ends in bounded time
             const u32 fb = full0 + 8u * b, fp = (s / kPanelStages) & 1u;
+            bool released = false;
             if (timed_out ? mbar_wait<1>(fb, fp) : mbar_wait(fb, fp)) {
-                const uint2 st = desc[b];
+                const uint4 st = desc[b];
+                const u32 nl = st.x >> 3, nlg = st.y >> 3, lpg = (st.z & 0xffffu) >> 3, lpp = (st.z >> 16) >> 3;
                 const unsigned char *sb = ebuf + b * EB;
-                const unsigned char *xs = panel_smem + st.y * PX;
-                for (u32 ib = kPanelPerThread * t; ib < st.x; ib += kPanelPerThread * kPanelConsumers) {
-                    u32 e[8], v[8];
-                    const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * ib);
-                    const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * ib + 16);
-                    e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
-                    e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
-                    if (SMALL) {
-                        const uint4 w = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 2 * ib);
-                        v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
-                        v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
-                    } else {
-                        const uint4 w0 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib);
-                        const uint4 w1 = *reinterpret_cast<const uint4 *>(sb + 4 * P.pe + 4 * ib + 16);
-                        v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
-                        v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
-                    }
+                const unsigned char *vb = sb + 4 * P.pe;
+                const unsigned char *xs = panel_smem + st.w * PX;
+                // the stage's 32-lane blocks start at a warp that moves on by a
+                // full stage's blocks from one stage to the next, so that
+                // consecutive stages run on different warps when there are
+                // more warps than blocks
+                const u32 w0 = ((u32)warp + kWarps - (s * rot) % kWarps) % kWarps;
+                for (u32 lb = w0 * 32u; lb < nl; lb += 32u * kWarps) {
+                    const u32 tl = lb + lane, c = min(32u, nl - lb);
+                    const bool valid = tl < nl, general = tl < nlg;
+                    u32 e[8];
                     AT tm[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & ((1u << kPanelColBits) - 1)));
-                        tm[u] = SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
+                        e[u] = 0;
+                        tm[u] = 0;
                     }
-                    if ((e[0] >> kPanelColBits) == (e[7] >> kPanelColBits)) {
-                        // rows ascend: all eight on one row (a long row), one addition
-                        atomicAdd(acc + (e[0] >> kPanelColBits),
-                                  ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7])));
-                    } else {
+                    if (valid) {
+                        // entries of lane j of this 32-lane block: 4j..4j+3 and 4c+4j..4c+4j+3
+                        const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * lane));
+                        const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * c + 4 * lane));
+                        e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
+                        e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
+                        if (general) {
+                            u32 v[8];
+                            if (SMALL) {
+                                const uint4 w = *reinterpret_cast<const uint4 *>(vb + 2 * 8 * tl);
+                                v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
+                                v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
+                            } else {
+                                const u32 cg = min(32u, nlg - lb);
+                                const uint4 w0 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * lane));
+                                const uint4 w1 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * cg + 4 * lane));
+                                v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
+                                v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
+                            }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> kPanelColBits), tm[u]);
+                            for (int u = 0; u < 8; ++u) {
+                                const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
+                                tm[u] = SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
+                            }
+                        } else {
+                            // +-1 sections (Sec. 2.4.2): x or m - x, no value
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
+                                tm[u] = (AT)((e[u] & kPanelNeg) ? M.m - xv : xv);
+                            }
+                        }
+                    }
+                    // the warp's last lanes of this stage are in registers (the terms
+                    // above read every loaded word): the buffer can be refilled
+                    // while the sums go on
+                    if (lb + 32u * kWarps >= nl) {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty0 + 8u * b);
+                        released = true;
+                    }
+                    const bool pack = valid && (general ? tl < lpg : tl - nlg < lpp);
+                    // packs sit in lanes [0, lpg) and [nlg, nlg + lpp): a warp-uniform test
+                    if (lb < lpg || (lb + 32u > nlg && lb < nlg + lpp)) {
+                        // segmented warp sum over the lanes of one row, then one atomic.
+                        // Packs of one row are adjacent within each section; a row
+                        // can have packs in both sections, so the +-1 packs get keys
+                        // of their own (the runs the sum joins must be contiguous)
+                        AT sum = 0;
+                        if (pack) sum = ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7]));
+                        const u32 key = pack ? ((e[0] >> 16) | (general ? 0u : 0x20000u)) : (0x10000u + (u32)lane);
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const AT o = __shfl_down_sync(0xffffffffu, sum, d);
+                            const u32 k2 = __shfl_down_sync(0xffffffffu, key, d);
+                            if (lane + d < 32 && k2 == key) sum += o;
+                        }
+                        const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
+                        if (pack && (lane == 0 || kp != key)) atomicAdd(acc + (key & 0xffffu), sum);
+                    }
+                    if (valid && !pack) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> 16), tm[u]);
                     }
                 }
             } else {
                 timed_out = true;
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty0 + 8u * b);
+            if (!released) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty0 + 8u * b);
+            }
         }
     }
     if (__syncthreads_or(timed_out)) {
-        // a copy or a buffer never came: report, and give the last copies a
-        // bounded chance to land before the CTA leaves
+        // a copy, a buffer or the grid barrier never came: report, and give
+        // the last copies a bounded chance to land before the CTA leaves
         if (t == 0) {
             if (status) atomicOr(status, 1);
             for (u32 s = ns > kPanelStages ? ns - kPanelStages : 0; s < ns; ++s)
@@ -775,12 +921,43 @@ k_panel(const PanelPart P, u32 *__restrict__ y, long long ldy, const Mod M, int 
         __syncthreads();
     }
     if (q > 1) cluster_sync_all();  // every partial sum of the cluster is final
-    const u32 share = (nr + q - 1) / q, rb = rank * share, re = min(nr, rb + share);
-    for (u32 r = rb + t; r < re; r += kPanelThreads) {
-        u64 sum = 0;
-        for (int j = 0; j < q; ++j) sum += (u64)(q > 1 ? ld_cluster(acc + r, (u32)j) : acc[r]);
-        u32 *yp = y + (long long)(r0 + r) * ldy;
-        *yp = combine(red64(sum, M), yp, false, M);
+    // This CTA finishes a share of the rows.  A thread takes G consecutive
+    // rows at a time: one 16-byte load of their partial sums from each CTA of
+    // the cluster, for three groups of rows, all issued before any is used
+    // (distributed shared memory answers slowly; loads in flight overlap).
+    constexpr u32 G = 16 / sizeof(AT);
+    const u32 share = ((nr + q - 1) / q + G - 1) / G * G;
+    const u32 rb = min(nr, rank * share), re = min(nr, rb + share);
+    for (u32 rg = rb + G * t; rg < re; rg += 3 * G * kPanelThreads) {
+        uint4 part[3][4];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const u32 r = rg + (u32)k * G * kPanelThreads;
+            if (r < re) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < q) part[k][j] = q > 1 ? ld_cluster_v4(acc + r, (u32)j) : *reinterpret_cast<const uint4 *>(acc + r);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const u32 r = rg + (u32)k * G * kPanelThreads;
+            if (r >= re) break;
+#pragma unroll
+            for (u32 i = 0; i < G; ++i) {
+                if (r + i >= re) break;
+                u64 sum = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j >= q) break;
+                    const uint4 w = part[k][j];
+                    const u32 c[4] = {w.x, w.y, w.z, w.w};
+                    sum += SMALL ? (u64)c[i] : ((u64)c[2 * i + 1] << 32 | c[2 * i]);
+                }
+                u32 *yp = y + (long long)(r0 + r + i) * ldy;
+                *yp = combine(red64(sum, M), yp, false, M);
+            }
+        }
     }
     if (q > 1) cluster_sync_all();  // no CTA leaves while its sums are being read
 }
@@ -816,20 +993,27 @@ int panel_max_clusters(bool small, int q, size_t smem)
     return n;
 }
 
+// The panel kernel stages x itself when all its CTAs are resident at once
+// (one row group per resident cluster); otherwise a staging launch runs first.
+static bool panel_fused(const PanelPart &pp) { return pp.ngroup <= pp.resident; }
+
 static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *y, long long ldy,
                                int vcol, const Mod &M, cudaStream_t st, const PanelCtl *ctl)
 {
     const PanelPart &pp = P.panel;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned sb =
-        (unsigned)std::max<long long>(1, std::min<long long>((P.ncols / 4 + 255) / 256, 8LL * std::max(nsm, 1)));
-    if (pp.small)
-        k_x_stage<unsigned short><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned short *)pp.xh);
-    else
-        k_x_stage<u32><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (u32 *)pp.xh);
-    FF_CUDA(cudaGetLastError());
+    const int fused = panel_fused(pp) ? 1 : 0;
+    if (!fused) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned sb =
+            (unsigned)std::max<long long>(1, std::min<long long>((P.ncols / 4 + 255) / 256, 8LL * std::max(nsm, 1)));
+        if (pp.small)
+            k_x_stage<unsigned short><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned short *)pp.xh);
+        else
+            k_x_stage<u32><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (u32 *)pp.xh);
+        FF_CUDA(cudaGetLastError());
+    }
     if (pp.small) panel_set_smem<true>(pp.smem);
     else panel_set_smem<false>(pp.smem);
     cudaLaunchConfig_t cfg = {};
@@ -837,21 +1021,19 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
     cfg.dynamicSmemBytes = pp.smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)pp.q;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    // start while the staging launch runs; its copying warp waits for it
-    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 1;
     u32 *yv = y + vcol;
+    const u32 *xv = x + vcol;
     int *status = ctl ? ctl->status : nullptr;
     const int skip = ctl ? ctl->skip_stage : -1;
-    if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, yv, ldy, M, status, skip));
-    else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, yv, ldy, M, status, skip));
+    if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, xv, ldx, yv, ldy, M, status, skip, fused));
+    else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, xv, ldx, yv, ldy, M, status, skip, fused));
     return FFSPMV_OK;
 }
 
@@ -864,7 +1046,7 @@ static int next_chunk(int left, bool has_atomic)
 long long count_plan_launches(const Plan &P, int nvec)
 {
     if (P.nrows == 0) return 0;
-    long long n = P.panel.on ? 2LL * nvec : 0;
+    long long n = P.panel.on ? (P.panel.ngroup <= P.panel.resident ? 1LL : 2LL) * nvec : 0;
     for (const Phase &ph : P.phases) {
         if (ph.segs.empty()) continue;
         for (int c0 = 0; c0 < nvec; c0 += next_chunk(nvec - c0, ph.has_atomic))

@@ -635,215 +635,51 @@ BinChoice heuristic_bin_choice(int b, double pm_fraction, int use_pm1)
     return c;
 }
 
-// x-panel layout.  The cluster size q (column groups) is the one that needs
-// the fewest waves of clusters, then keeps the most SMs busy, then splits x
-// the most; the row groups, one per resident cluster, are balanced by entries
-// under the shared-memory row cap.  Column groups are balanced by entries too,
-// with boundaries on multiples of 8 columns (16-byte aligned panel copies).
-// The shared memory left after the row sums is cut into kPanelStages stages,
-// each split between x and entries in the ratio the matrix's density asks
-// for.  Rows longer than kPanelLong are left out; the caller gives them split
-// CSR segments that add into y.
-struct PanelLayout {
-    std::vector<u32> grp_row0, stage_ptr;
-    std::vector<PanelStage> stage;
-};
-
-static std::vector<u32> panel_row_groups(const Mat &A, long long nnz, long long groups, long long rcap,
-                                         const std::function<long long(long long)> &len)
+// x-panel layout: the host half (geometry, stages, entry order) is
+// panel_layout (panel.cu); this puts it into the plan's arena.
+bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPart &pp, size_t &o_grp,
+                size_t &o_sptr, size_t &o_stage, size_t &o_ent, size_t &o_val, size_t &o_xh, size_t &o_bar)
 {
-    std::vector<u32> row0{0};
-    const long long target = std::max<long long>(1, (nnz + groups - 1) / groups);
-    long long cur = 0;
-    for (long long i = 0; i < A.nrows; ++i) {
-        const long long rows = i - row0.back();
-        if (rows > 0 && (rows >= rcap || cur >= target)) {
-            row0.push_back((u32)i);
-            cur = 0;
-        }
-        cur += len(i);
+    long long npm = 0;
+    for (auto c : A.cls) npm += c != 0;
+    const long long nnz = (long long)A.col.size();
+    // +-1 sections: forced on or off by use_pm1, else when +-1 entries are
+    // at least 5% of the matrix
+    const bool pm_on = use_pm1 == 1 || (use_pm1 < 0 && nnz > 0 && npm * 20 >= nnz);
+    PanelHost H;
+    if (!panel_layout(A.nrows, A.ncols, A.ptr.data(), A.col.data(), A.val.data(), A.cls.data(), m, pm_on,
+                      force_q, [](int q, bool small) { return panel_max_clusters(small, q, kPanelSmemMax); }, H))
+        return false;
+    const int vb = H.small ? 2 : 4, xb = H.small ? 2 : 4;
+    std::vector<unsigned char> vbytes(H.val.size() * vb + 64, 0);
+    for (size_t t = 0; t < H.val.size(); ++t) {
+        if (vb == 2) ((unsigned short *)vbytes.data())[t] = (unsigned short)H.val[t];
+        else ((u32 *)vbytes.data())[t] = H.val[t];
     }
-    row0.push_back((u32)A.nrows);
-    return row0;
-}
-
-bool make_panel(Blob &B, const Mat &A, u32 m, PanelPart &pp, size_t &o_grp, size_t &o_sptr,
-                size_t &o_stage, size_t &o_ent, size_t &o_val, size_t &o_xh)
-{
-    const long long n = A.nrows, nc = A.ncols;
-    const std::function<long long(long long)> len = [&](long long i) {
-        const long long L = A.ptr[i + 1] - A.ptr[i];
-        return L > kPanelLong ? 0LL : L;
-    };
-    long long nnz = 0;
-    for (long long i = 0; i < n; ++i) nnz += len(i);
-    if (n <= 0 || nc <= 0 || nnz == 0 || nnz >= (1LL << 31) || nc >= (1LL << 31) - 65536) return false;
-    const bool small = m <= 65536u;
-    const int xb = small ? 2 : 4, vb = small ? 2 : 4, ab = small ? 4 : 8;
-    const int ebytes = 4 + vb;
-    const int min_sb = 8192 + 1024 * ebytes;
-    const long long rcap = std::min<long long>(1LL << (32 - kPanelColBits),
-                                               (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
-                                                kPanelStages * min_sb) / ab);
-
-    // cluster size: fewest waves, then most CTAs busy, then larger q
-    int q = 0, nclus = 0;
-    long long best_waves = 0, best_used = 0;
-    std::vector<u32> row0;
-    for (int cq : {1, 2, 4}) {
-        if (cq > 1 && nc < 2LL * cq * 8192) break;
-        const int c = panel_max_clusters(small, cq, kPanelSmemMax);
-        if (c <= 0) continue;
-        std::vector<u32> r = panel_row_groups(A, nnz, c, rcap, len);
-        const long long G = (long long)r.size() - 1;
-        const long long waves = (G + c - 1) / c, used = std::min<long long>(G, c) * cq;
-        if (q == 0 || waves < best_waves || (waves == best_waves && used >= best_used)) {
-            q = cq;
-            nclus = c;
-            best_waves = waves;
-            best_used = used;
-            row0.swap(r);
-        }
-    }
-    if (q == 0) return false;
-    const long long ng = (long long)row0.size() - 1;
-    long long rows_max = 1;
-    for (long long g = 0; g < ng; ++g) rows_max = std::max<long long>(rows_max, row0[g + 1] - row0[g]);
-
-    // column groups
-    std::vector<long long> ccount((size_t)nc, 0);
-    for (long long i = 0; i < n; ++i)
-        if (len(i))
-            for (long long k = A.ptr[i]; k < A.ptr[i + 1]; ++k) ccount[A.col[k]]++;
-    std::vector<long long> cb{0};
-    {
-        long long cur = 0;
-        for (long long c = 0; c < nc && (int)cb.size() < q; ++c) {
-            cur += ccount[c];
-            if (cur * q >= nnz * (long long)cb.size() && (c + 1) % 8 == 0 && c + 1 < nc) cb.push_back(c + 1);
-        }
-        while ((int)cb.size() < q) cb.push_back(nc);  // empty trailing groups
-        cb.push_back(nc);
-    }
-    // stage geometry
-    long long W = 8;
-    for (int j = 0; j < q; ++j) W = std::max<long long>(W, cb[j + 1] - cb[j]);
-    const long long acc_bytes = (rows_max * ab + 15) / 16 * 16;
-    const long long sb =
-        (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes - acc_bytes) / kPanelStages / 16 * 16;  // x slot + entries
-    const double dens = (double)nnz / ((double)ng * q) / (double)W;  // entries per column of a CTA
-    long long pcols = (long long)((double)sb / ((double)xb + 1.15 * ebytes * dens));
-    pcols = std::min<long long>({pcols, (1LL << kPanelColBits) / xb, (W + 7) / 8 * 8});
-    pcols = std::max<long long>(8, pcols / 8 * 8);
-    const long long pe = std::min<long long>((sb - pcols * xb) / ebytes / 8 * 8, 1LL << 20);
-    if (pe < 8) return false;
-    const long long eb = pe * ebytes;  // a multiple of 16
-    const size_t smem = (size_t)(kPanelStages * (pcols * xb + eb) + kPanelBarBytes + kPanelDescBytes + acc_bytes);
-
-    std::vector<long long> pbase(q + 1, 0);  // global panel ids by group
-    for (int j = 0; j < q; ++j) pbase[j + 1] = pbase[j] + std::max<long long>(1, (cb[j + 1] - cb[j] + pcols - 1) / pcols);
-    const long long npan = pbase[q];
-    std::vector<int> cgrp((size_t)nc);
-    std::vector<u32> cpan((size_t)nc);
-    for (int j = 0; j < q; ++j)
-        for (long long c = cb[j]; c < cb[j + 1]; ++c) {
-            cgrp[c] = j;
-            cpan[c] = (u32)(pbase[j] + (c - cb[j]) / pcols);
-        }
-
-    if (ng * npan >= (1LL << 31)) return false;
-
-    // entries bucketed by (row group, panel), rows ascending within a bucket
-    std::vector<long long> bstart((size_t)(ng * npan + 1), 0);
-    for (long long g = 0; g < ng; ++g)
-        for (long long i = row0[g]; i < row0[g + 1]; ++i)
-            if (len(i))
-                for (long long k = A.ptr[i]; k < A.ptr[i + 1]; ++k) bstart[g * npan + cpan[A.col[k]] + 1]++;
-    for (size_t t = 1; t < bstart.size(); ++t) bstart[t] += bstart[t - 1];
-    std::vector<u32> bent((size_t)nnz), bval((size_t)nnz);
-    {
-        std::vector<long long> pos(bstart.begin(), bstart.end() - 1);
-        for (long long g = 0; g < ng; ++g)
-            for (long long i = row0[g]; i < row0[g + 1]; ++i) {
-                if (!len(i)) continue;
-                for (long long k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-                    const long long c = A.col[k], pan = cpan[c];
-                    const long long xoff = cb[cgrp[c]] + (pan - pbase[cgrp[c]]) * pcols;
-                    const long long at = pos[g * npan + pan]++;
-                    bent[at] = ((u32)(i - row0[g]) << kPanelColBits) | (u32)((c - xoff) * xb);
-                    bval[at] = A.val[k];
-                }
-            }
-    }
-
-    // stages, CTA by CTA; each padded to a multiple of 8 entries with zero
-    // terms on its last row
-    PanelLayout L;
-    L.grp_row0 = row0;
-    L.stage_ptr.push_back(0);
-    std::vector<u32> ent;
-    std::vector<u32> val;
-    ent.reserve((size_t)nnz + 8 * (size_t)(ng * npan));
-    val.reserve((size_t)nnz + 8 * (size_t)(ng * npan));
-    for (long long g = 0; g < ng; ++g)
-        for (int j = 0; j < q; ++j) {
-            const long long np = pbase[j + 1] - pbase[j], rot = g * np / ng;
-            u32 loaded = 0;  // panels copied in so far
-            for (long long t0 = 0; t0 < np; ++t0) {
-                const long long pan = pbase[j] + (t0 + rot) % np;
-                const long long b0 = bstart[g * npan + pan], b1 = bstart[g * npan + pan + 1];
-                const u32 xoff = (u32)(cb[j] + (pan - pbase[j]) * pcols);
-                for (long long k = b0; k < b1; k += pe) {
-                    const long long e = std::min<long long>(b1, k + pe);
-                    PanelStage st;
-                    st.xoff = xoff;
-                    // a new panel takes the slot of the panel three back, whose
-                    // stages all ended before the previous two panels' stages
-                    st.xs = (loaded % kPanelStages) | (k == b0 ? 4u : 0u);
-                    st.k0 = (u32)ent.size();
-                    for (long long t = k; t < e; ++t) {
-                        ent.push_back(bent[t]);
-                        val.push_back(bval[t]);
-                    }
-                    const u32 last = bent[e - 1] & ~((1u << kPanelColBits) - 1);
-                    while (ent.size() % 8) {
-                        ent.push_back(last);
-                        val.push_back(0);
-                    }
-                    st.nent = (u32)(ent.size() - st.k0);
-                    L.stage.push_back(st);
-                }
-                if (b1 > b0) ++loaded;
-            }
-            L.stage_ptr.push_back((u32)L.stage.size());
-        }
-    if (ent.size() >= (1ull << 32)) return false;
-    if (L.stage.empty()) L.stage.push_back(PanelStage{0, 0, 0, 0});
-    std::vector<unsigned char> vbytes(val.size() * vb + 64, 0);
-    for (size_t t = 0; t < val.size(); ++t) {
-        if (vb == 2) ((unsigned short *)vbytes.data())[t] = (unsigned short)val[t];
-        else ((u32 *)vbytes.data())[t] = val[t];
-    }
-    ent.resize(ent.size() + 16, 0);
-
+    H.ent.resize(H.ent.size() + 16, 0);
     pp.on = true;
-    pp.small = small;
-    pp.q = q;
-    pp.ngroup = (int)ng;
-    pp.rows_max = (int)rows_max;
-    pp.resident = nclus;
-    pp.px = (int)(pcols * xb);
-    pp.pe = (int)pe;
-    pp.eb = (int)eb;
-    pp.nstage = (long long)L.stage.size();
-    pp.smem = smem;
-    o_grp = B.putv(L.grp_row0);
-    o_sptr = B.putv(L.stage_ptr);
-    o_stage = B.putv(L.stage);
-    o_ent = B.putv(ent);
+    pp.small = H.small;
+    pp.q = H.q;
+    pp.ngroup = H.ngroup;
+    pp.rows_max = H.rows_max;
+    pp.resident = H.resident;
+    pp.px = H.px;
+    pp.pe = H.pe;
+    pp.eb = H.eb;
+    pp.ncols = A.ncols;
+    pp.nstage = H.nstage;
+    pp.npm = H.npm;
+    pp.npad = H.npad;
+    pp.smem = H.smem;
+    o_grp = B.putv(H.grp_row0);
+    o_sptr = B.putv(H.stage_ptr);
+    o_stage = B.putv(H.stage);
+    o_ent = B.putv(H.ent);
     o_val = B.putv(vbytes);
-    std::vector<unsigned char> z((size_t)(nc + pcols + 64) * xb, 0);
+    std::vector<unsigned char> z((size_t)(A.ncols + H.pcols + 64) * xb, 0);
     o_xh = B.putv(z);
+    std::vector<u32> bar(2, 0);
+    o_bar = B.putv(bar);
     return true;
 }
 
@@ -1049,8 +885,9 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
     }
     case FFSPMV_FMT_PANEL: {
         name = "PANEL";
-        size_t o_grp, o_sptr, o_stage, o_ent, o_val, o_xh;
-        if (make_panel(B, A, m, P.panel, o_grp, o_sptr, o_stage, o_ent, o_val, o_xh)) {
+        size_t o_grp, o_sptr, o_stage, o_ent, o_val, o_xh, o_bar;
+        if (make_panel(B, A, m, upm, opt.panel_cluster, P.panel, o_grp, o_sptr, o_stage, o_ent, o_val, o_xh,
+                       o_bar)) {
             // rows beyond kPanelLong: split CSR segments adding into y after the panels
             Rows huge;
             for (long long i = 0; i < nrows; ++i)
@@ -1078,13 +915,14 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
         P.panel.ent = (const u32 *)(base + o_ent);
         P.panel.val = base + o_val;
         P.panel.xh = base + o_xh;
+        P.panel.gbar = (u32 *)(base + o_bar);
         describe(P, name);
-        char buf[320];
+        char buf[400];
         snprintf(buf, sizeof buf,
                  "  panels: %d row groups x %d column groups (clusters of %d, %d resident), %lld stages of %d B x"
-                 " + %d entries, x staged as %s, %s row sums\n",
+                 " + %d entries, x staged as %s, %s row sums, %lld entries in +-1 sections, %lld padding\n",
                  P.panel.ngroup, P.panel.q, P.panel.q, P.panel.resident, P.panel.nstage, P.panel.px, P.panel.pe,
-                 P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64");
+                 P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64", P.panel.npm, P.panel.npad);
         P.summary += buf;
         return FFSPMV_OK;
     }

@@ -108,6 +108,26 @@ def test_panel_clusters(lib, m):
     M.check_status()  # no bounded wait ran out
 
 
+def test_panel_packs_in_both_sections(lib):
+    # rows with eight general and eight +-1 entries in one stage: a general
+    # pack and a +-1 pack of one row in the same warp, single lanes between
+    rng = np.random.default_rng(9)
+    n, m = 300, 65521
+    cols, vals, rp = [], [], [0]
+    for i in range(n):
+        k = 16 if i % 7 == 0 else int(rng.integers(1, 12))
+        c = np.sort(rng.choice(n, k, replace=False))
+        v = rng.integers(2, m - 1, k)
+        if i % 7 == 0:
+            v[::2] = np.where(rng.random(8) < 0.5, 1, m - 1)
+        cols.append(c); vals.append(v); rp.append(rp[-1] + k)
+    A = gen.CSR(n, n, np.array(rp, np.int64), np.concatenate(cols).astype(np.int32),
+                np.concatenate(vals).astype(np.uint32), m)
+    M = make(lib, A, "PANEL", use_pm1=1)
+    check_apply(lib, M, A, seed=41)
+    check_apply(lib, M, A, alpha=3, beta=5, transpose=True, seed=42)
+
+
 def test_panel_timeout_hook_sets_status_and_handle_survives(lib):
     # the copies of each CTA's second stage are never issued: the bounded
     # waits for them run out, the kernel ends, and the status word says so
@@ -125,21 +145,25 @@ def test_panel_timeout_hook_sets_status_and_handle_survives(lib):
     check_apply(lib, N, A, seed=4)
 
 
-def test_panel_longest_rows_worst_values(lib):
-    # m <= 2^16: terms are reduced only below 2m, so a row sum of 32 768 terms
-    # is the most a 32-bit shared-memory sum holds; longer rows leave the
-    # panels.  Every value and every x is m - 1 (the largest terms).
+@pytest.mark.parametrize("use_pm1", [0, 1])
+def test_panel_longest_rows_worst_values(lib, use_pm1):
+    # m <= 2^16: general terms are reduced only below 2m, and a -1 entry's
+    # term is m - x <= m, so a row sum of 32 768 terms is the most a 32-bit
+    # shared-memory sum holds; longer rows leave the panels.  Every value is
+    # m - 1: with +-1 sections off these are the largest general terms (x =
+    # m - 1), with them on the largest -1 terms (x = 0).
     m = 65521
     lengths = np.array([32_768, 32_769, 40_000, 5, 0, 1])
     n, nc = lengths.size, 100_000
     col = np.concatenate([np.arange(L) * 2 for L in lengths]).astype(np.int32)
     A = gen.CSR(n, nc, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col,
                 np.full(lengths.sum(), m - 1, dtype=np.uint32), m)
-    M = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE)
+    M = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE, use_pm1=use_pm1)
     assert "panels:" in M.describe()
-    x = np.full(nc, m - 1, dtype=np.uint32)
+    xv = 0 if use_pm1 else m - 1
+    x = np.full(nc, xv, dtype=np.uint32)
     y = to_host(M.apply(to_dev(x)))
-    assert list(y) == [int(L) % m for L in lengths]
+    assert list(y) == [int(L) * (m - 1) * xv % m for L in lengths]
     check_apply(lib, M, A, alpha=2, beta=3, seed=6)
 
 
