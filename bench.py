@@ -627,7 +627,7 @@ def main():
     abytes = algorithmic_bytes(A, m)
     achieved = abytes / (ax_ms / 1e3) / 1e9
     fmt_a = M.describe().split(":")[0].split()[-1]
-    kname = ("k_panel (y=A*x; the interval also holds its k_x_stage launch)" if fmt_a == "PANEL"
+    kname = ("k_panel (y=A*x: one launch, x staged inside the kernel)" if fmt_a == "PANEL"
              else "k_plan (y=A*x)")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic_record(f"spmv_A_{m}_{fmt_a}"),

@@ -210,10 +210,10 @@ constexpr int kPanelBarBytes = 128;           // full and empty mbarrier of each
 constexpr int kPanelDescBytes = 128;          // (entries, general, packs, x slot) of each buffer
 constexpr u32 kPanelSlotMask = 7u;            // PanelStage::xs: x slot
 constexpr u32 kPanelNewX = 8u;                // PanelStage::xs: the panel is copied in with this stage
-static_assert(16 * kPanelStages <= kPanelBarBytes && kPanelStages <= 8, "mbarriers and slots of the stage buffers");
+static_assert(16 * kPanelStages + 8 <= kPanelBarBytes && kPanelStages <= 7,
+              "full and empty mbarriers of the stage buffers, the epilogue's receive mbarrier, x slots");
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
 constexpr unsigned kPanelGridSpin = 1u << 20; // polls of the grid barrier before giving up
-constexpr int kPanelAhead = 2;                // rounds of a buffer's stages pulled into L2 ahead of use
 constexpr u32 kPanelIdxMask = 0x7fffu;        // x element of the panel
 constexpr u32 kPanelNeg = 0x8000u;            // a -1 entry (+-1 sections)
 constexpr long long kPanelLong = 32768;       // longer rows go to split CSR segments
@@ -242,7 +242,7 @@ struct PanelPart {
     int q = 1;           // CTAs per cluster (column groups)
     int ngroup = 0;      // row groups
     int rows_max = 0;    // most rows in one group
-    int resident = 0;    // clusters of q resident at once
+    int resident = 0;    // clusters of q CTAs of the panel kernel resident at once
     int px = 0;          // bytes of x per panel (a multiple of 128)
     int pe = 0;          // entry capacity of a stage (a multiple of 8)
     int eb = 0;          // bytes per stage's entry buffer (a multiple of 128)

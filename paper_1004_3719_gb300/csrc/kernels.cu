@@ -561,22 +561,6 @@ __device__ __forceinline__ uint4 ld_cluster_v4(const T *local, u32 rank)
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T ld_cluster(const T *local, u32 rank)
-{
-    u32 a = (u32)__cvta_generic_to_shared(local), r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    if constexpr (sizeof(T) == 4) {
-        u32 v;
-        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(r) : "memory");
-        return v;
-    } else {
-        u64 v;
-        asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(r) : "memory");
-        return v;
-    }
-}
-
 // A value in [0, 2m) congruent to t mod m, for t < 2^32 and mu = floor(2^32 / m):
 // the quotient estimate floor(t * mu / 2^32) is floor(t/m) or one less
 // (Barrett, 1986); the last conditional subtraction is left to the row sum's
@@ -607,12 +591,6 @@ __device__ __forceinline__ void bulk_g2s(u32 dst, const void *src, u32 bytes, u3
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
-}
-
-// Start pulling `bytes` at `src` into L2 (no completion to wait for).
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, u32 bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Wait for the phase of `bar` with parity `parity`; false after POLLS polls.
@@ -684,6 +662,10 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     const u32 full0 = (u32)__cvta_generic_to_shared(bars), empty0 = full0 + 8u * kPanelStages;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
+    // the grid barrier's generation before this CTA arrives (read early: the
+    // load overlaps the conversion below)
+    u32 g0 = 0;
+    if (fused && t == 0) g0 = ld_acquire_gpu(P.gbar + 1);
     if (fused) {
         // this CTA's share of x, converted into the staged copy that every
         // CTA's bulk copies read
@@ -729,10 +711,10 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::: "memory");
         if (fused) {
             // grid barrier: arrivals in gbar[0], generation in gbar[1]; the
-            // last CTA to arrive resets the count and moves the generation on
-            const u32 g0 = ld_acquire_gpu(P.gbar + 1);
+            // last CTA to arrive resets the count and moves the generation on.
+            // The release of the arrival covers the CTA's conversion stores
+            // (ordered before it by the barrier above)
             s_gen = g0;
-            __threadfence();
             if (atom_add_release_gpu(P.gbar, 1u) == gridDim.x - 1) {
                 atomicExch(P.gbar, 0u);
                 st_release_gpu(P.gbar + 1, g0 + 1);
@@ -756,17 +738,6 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
         const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
         bool xready = !fused;
-        // lane 2 pulls the entries and values of this buffer's later stages
-        // into L2 (HBM latency is long; the stage buffers hold little of it)
-        auto prefetch = [&](u32 s) {
-            if (s < ns) {
-                const PanelStage a = P.stage[s0 + s];
-                bulk_prefetch_l2(ev + (size_t)a.k0 * 4, a.nent * 4u);
-                if (a.ngen) bulk_prefetch_l2(vv + (size_t)a.v0 * VB, a.ngen * (u32)VB);
-            }
-        };
-        if (lane == 2)
-            for (u32 k = 1; k <= (u32)kPanelAhead; ++k) prefetch(b + k * kPanelStages);
         for (u32 s = b; s < ns; s += kPanelStages) {
             const PanelStage a = P.stage[s0 + s];
             if (s >= kPanelStages) {
@@ -786,7 +757,6 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
                 if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, a.ngen * (u32)VB, bar);
             }
-            if (lane == 2) prefetch(s + (kPanelAhead + 1) * kPanelStages);
             if (lane == 0) {
                 if (!xready) {
                     // every CTA's share of x is staged before the first panel copy
@@ -936,7 +906,9 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
             if (r < re) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (j < q) part[k][j] = q > 1 ? ld_cluster_v4(acc + r, (u32)j) : *reinterpret_cast<const uint4 *>(acc + r);
+                    if (j < q)
+                        part[k][j] = (q > 1 && j != rank) ? ld_cluster_v4(acc + r, (u32)j)
+                                                          : *reinterpret_cast<const uint4 *>(acc + r);
             }
         }
 #pragma unroll

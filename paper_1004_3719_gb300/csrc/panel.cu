@@ -312,7 +312,9 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     const long long rcap = std::min<long long>(65536, (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
                                                        kPanelStages * min_sb) / ab);
 
-    // cluster size: fewest waves, then most CTAs busy, then larger q
+    // cluster size (column groups): the fewest waves of clusters, then the
+    // most SMs busy, then the larger q; row groups, one per resident
+    // cluster, balanced by entries under the shared-memory row cap
     int q = 0, nclus = 0;
     long long best_waves = 0, best_used = 0;
     std::vector<u32> row0;

@@ -678,7 +678,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPar
     o_val = B.putv(vbytes);
     std::vector<unsigned char> z((size_t)(A.ncols + H.pcols + 64) * xb, 0);
     o_xh = B.putv(z);
-    std::vector<u32> bar(2, 0);
+    std::vector<u32> bar(2, 0);  // grid barrier: arrivals, generation
     o_bar = B.putv(bar);
     return true;
 }

@@ -95,14 +95,18 @@ def test_split_long_rows(lib):
             check_apply(lib, M, A, nvec=3, seed=pm + 2)
 
 
-@pytest.mark.parametrize("m", [65521, 2**31 - 1])
-def test_panel_clusters(lib, m):
-    # enough columns for clusters of 2-4 CTAs splitting the columns; the
+@pytest.mark.parametrize("m,q", [(65521, 0), (65521, 1), (65521, 2), (65521, 4),
+                                 (2**31 - 1, 0), (2**31 - 1, 1), (2**31 - 1, 2)])
+def test_panel_column_groups(lib, m, q):
+    # clusters of 1, 2 or 4 CTAs splitting the columns (0: the builder's
+    # choice; with u64 row sums four column groups leave no room); the
     # transpose has the power-law skew on its columns instead of its rows
     A = gen.powerlaw_matrix(seed=8, n=150_001, lmax=20_000, m=m, pm_fraction=0.2)
-    M = make(lib, A, "PANEL")
-    assert "clusters of" in M.describe()
-    check_apply(lib, M, A, alpha=7, beta=5, seed=31)
+    M = make(lib, A, "PANEL", panel_cluster=q)
+    if q:
+        assert f"x {q} column groups" in M.describe()
+    for rep in range(2):  # the group counters carry over between calls
+        check_apply(lib, M, A, alpha=7, beta=5, seed=31 + rep)
     check_apply(lib, M, A, transpose=True, seed=32)
     check_apply(lib, M, A, nvec=2, seed=33)
     M.check_status()  # no bounded wait ran out
