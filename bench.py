@@ -304,8 +304,9 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
                 key = f if pm < 0 else f"{f}{'+pm1' if pm else '-nopm1'}"
                 try:
                     if f in sel_of:
-                        # the selector's per-bin choices, in the binned layout
-                        M = ff.Matrix.from_csr(A, selector=sel_of[f], priority_format=ff.FMT.BINNED,
+                        # FMT.AUTO under that selector: it picks the layout
+                        # (x-panel or binned) and the per-bin formats
+                        M = ff.Matrix.from_csr(A, selector=sel_of[f], priority_format=ff.FMT.AUTO,
                                                transpose_mode=ff.TRANSPOSE.NONE, use_pm1=pm)
                     else:
                         M = ff.Matrix.from_csr(A, priority_format=getattr(ff.FMT, f),
@@ -321,6 +322,8 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
                 row[key] = {"gnnz_s": round(A.nnz / ms / 1e6, 1),
                             "gbs": round(algorithmic_bytes(A, m) / ms / 1e6, 1),
                             "ms": round(ms, 4)}
+                if f in sel_of or f == "AUTO":
+                    row[key]["layout"] = "panel" if "panels" in M.describe() else "binned"
                 del M
         out[f"m={m}"] = row
     return out

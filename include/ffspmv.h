@@ -43,10 +43,16 @@ typedef enum {
     FFSPMV_ERR_TIMEOUT = 6      /* a bounded device wait expired (grid barrier) */
 } ffspmv_status;
 
-/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO is the x-panel layout
- * when m <= 2^16, nnz >= 2^21 and nnz >= 3 * ncols (decided separately for A
- * and A^T), else the binned layout with the bin formats picked by
- * opt.selector. */
+/* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO, decided separately
+ * for A and A^T, by opt.selector:
+ *   HEURISTIC (and FIXED): the x-panel layout when m <= 2^16, nnz >= 2^21
+ *     and nnz >= 3 * ncols, else the binned layout with the heuristic table;
+ *   LEARNED: the layout of least predicted whole-plan time among x-panel,
+ *     binned with the network's per-bin table and binned with the heuristic
+ *     table (the network's matrix-level outputs); without installed weights,
+ *     the exhaustive bins and the HEURISTIC panel rule;
+ *   EXHAUSTIVE: times the x-panel plan and the binned plan of the per-bin
+ *     winners on the device and keeps the faster. */
 enum {
     FFSPMV_FMT_AUTO = 0,
     FFSPMV_FMT_CSR = 1,     /* plain CSR, one fixed thread-group width per row */
@@ -122,11 +128,11 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
  * beta y and its block form).  d_x: ncols x nvec (ldx), d_y: nrows x nvec
  * (ldy); 1 <= nvec; alpha, beta < m (reduced if not).  beta = 0 never reads
  * d_y ("apply": y <- A x).  d_x and d_y must not overlap.  On a handle whose
- * plan is the x-panel layout, a block of 3 or more vectors runs a binned plan
- * that reads the matrix once for the whole block (Sec. 2.5.1); the first
- * such call builds that plan (synchronous, allocates once per handle and
- * direction).  Calls on one handle must not overlap on the GPU (the x-panel
- * plan stages x in a buffer of the handle).
+ * plan is the x-panel layout, a block runs one panel pass per vector (a
+ * binned plan that reads the matrix once per block measured 2.5 to 3 times
+ * slower per vector on the 1M x 1M power-law matrix).  Calls on one handle
+ * must not overlap on the GPU (the x-panel plan stages x in a buffer of the
+ * handle).
  */
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx,
                          uint32_t *d_y, int64_t ldy, int32_t nvec,
@@ -226,8 +232,7 @@ ffspmv_status spmv_describe_plan(ffspmv_t h, char *buf, size_t len);
 
 /* Number of kernel launches that one spmv_apply (transpose = 0) or
  * spmv_apply_transpose (transpose = 1) call with nvec vectors enqueues
- * (for a wide block on an x-panel handle this builds the binned plan that
- * the call would use, as spmv_apply does). */
+ * (host arithmetic only, nothing is enqueued). */
 ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec,
                                   int64_t *launches);
 

@@ -33,7 +33,17 @@ extern "C" {
 #define FFSPMV_NUM_BIN_FEATURES 6  /* per bin */
 #define FFSPMV_MLP_IN (FFSPMV_NUM_FEATURES + FFSPMV_NUM_BIN_FEATURES)
 #define FFSPMV_MLP_HIDDEN 64
-#define FFSPMV_MLP_OUT (FFSPMV_NUM_FORMATS + 1) /* format scores + log(t_pm / t_nopm) */
+/* outputs: the formats' predicted log(t_format / t_best) and log(t_pm / t_nopm)
+ * for a (matrix, bin) input; for the matrix-level input (the bin features all
+ * FFSPMV_MATRIX_INPUT) the predicted whole-plan log(t / t_binned) of the
+ * binned layout with the network's table and of the x-panel layout with
+ * clusters of 1, 2 and 4 CTAs, t_binned being the binned layout with the
+ * heuristic table */
+#define FFSPMV_MLP_OUT (FFSPMV_NUM_FORMATS + 5)
+#define FFSPMV_OUT_PM FFSPMV_NUM_FORMATS
+#define FFSPMV_OUT_NETBINS (FFSPMV_NUM_FORMATS + 1)
+#define FFSPMV_OUT_PANEL (FFSPMV_NUM_FORMATS + 2) /* q = 1; q = 2 and 4 follow */
+#define FFSPMV_MATRIX_INPUT (-1.0f) /* value of every bin feature of the matrix-level input */
 /* flat parameter vector: W1[H][IN] b1[H] W2[H][H] b2[H] W3[OUT][H] b3[OUT] */
 #define FFSPMV_MLP_PARAMS                                                  \
     (FFSPMV_MLP_HIDDEN * FFSPMV_MLP_IN + FFSPMV_MLP_HIDDEN +                \
@@ -100,10 +110,23 @@ ffspmv_status ffspmv_mlp_adam(float *d_params, const float *d_grad, float *d_m, 
 ffspmv_status ffspmv_selector_load(const float *params, int64_t count);
 
 /* The selector's choice for a matrix (host or device CSR): best[17][3] as in
- * ffspmv_tune_bins, from the network's inference kernel on the device. */
+ * ffspmv_tune_bins, from the network's inference kernel on the device, and
+ * (layout != NULL) the whole-plan choice of least predicted time:
+ * FFSPMV_LAYOUT_BINNED (the binned layout with the heuristic table),
+ * FFSPMV_LAYOUT_NETBINS (the binned layout with best[][]) or
+ * FFSPMV_LAYOUT_PANEL_Q1/Q2/Q4 (the x-panel layout with clusters of 1, 2 or
+ * 4 CTAs).  This is what FFSPMV_SEL_LEARNED builds under FFSPMV_FMT_AUTO. */
+enum {
+    FFSPMV_LAYOUT_BINNED = 0,
+    FFSPMV_LAYOUT_NETBINS = 1,
+    FFSPMV_LAYOUT_PANEL_Q1 = 2,
+    FFSPMV_LAYOUT_PANEL_Q2 = 3,
+    FFSPMV_LAYOUT_PANEL_Q4 = 4
+};
 ffspmv_status ffspmv_selector_choose(int64_t nrows, int64_t ncols, int64_t nnz,
                                      const int64_t *row_ptr, const int32_t *col,
-                                     const uint32_t *values, uint32_t modulus, int32_t *best);
+                                     const uint32_t *values, uint32_t modulus, int32_t *best,
+                                     int32_t *layout);
 
 /* The heuristic table's choice (host CSR: row_ptr, values), best[17][3] as
  * in ffspmv_tune_bins; use_pm1 as in ffspmv_options. */

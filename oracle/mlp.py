@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-IN, H, OUT = 22, 64, 11
+IN, H, OUT = 22, 64, 15
 
 
 def unpack(p):

@@ -115,7 +115,7 @@ EXTRA_SIGNATURES = [
     ("ffspmv_mlp_adam", [_P, _P, _P, _P, _I32, _F, _F, _F, _F, _P], ctypes.c_int),
     ("ffspmv_selector_load", [_P, _I64], ctypes.c_int),
     ("ffspmv_heuristic_choose", [_I64, _P, _P, _U32, _I32, _P], ctypes.c_int),
-    ("ffspmv_selector_choose", [_I64, _I64, _I64, _P, _P, _P, _U32, _P], ctypes.c_int),
+    ("ffspmv_selector_choose", [_I64, _I64, _I64, _P, _P, _P, _U32, _P, _P], ctypes.c_int),
     ("spmv_create_binned", [ctypes.POINTER(_P), _I64, _I64, _I64, _P, _P, _P, _U32, _P,
                             ctypes.POINTER(Options), _P], ctypes.c_int),
 ]
@@ -127,7 +127,12 @@ NUM_FEATURES = 16
 NUM_BIN_FEATURES = 6
 MLP_IN = NUM_FEATURES + NUM_BIN_FEATURES
 MLP_HIDDEN = 64
-MLP_OUT = NUM_FORMATS + 1
+MLP_OUT = NUM_FORMATS + 5
+OUT_PM = NUM_FORMATS            # log(t_pm / t_nopm) of a bin
+OUT_NETBINS = NUM_FORMATS + 1   # whole plan: log(t_binned_network / t_binned)
+OUT_PANEL = NUM_FORMATS + 2     # whole plan: log(t_panel_q / t_binned), q = 1, 2, 4
+MATRIX_INPUT = -1.0             # every bin feature of the matrix-level input
+LAYOUT_BINNED, LAYOUT_NETBINS, LAYOUT_PANEL_Q1, LAYOUT_PANEL_Q2, LAYOUT_PANEL_Q4 = range(5)
 MLP_PARAMS = (MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN
               + MLP_OUT * MLP_HIDDEN + MLP_OUT)
 SELECTOR_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.npy")

@@ -45,11 +45,6 @@ void destroy_handle(ffspmv_handle *h)
     if (!h) return;
     free_plan(h->A);
     free_plan(h->AT);
-    for (ff::Plan *&mp : h->multi) {
-        if (mp) free_plan(*mp);
-        delete mp;
-        mp = nullptr;
-    }
     if (h->scatter) cudaFree(h->scatter);
     if (h->csr_arena) cudaFree(h->csr_arena);
     if (h->d_status) cudaFree(h->d_status);
@@ -105,12 +100,13 @@ ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
                                   const u32 *val, u32 m, const ffspmv_options &o)
 {
     const bool exhaustive = o.selector == FFSPMV_SEL_EXHAUSTIVE;
-    if (o.priority_format == FFSPMV_FMT_AUTO && !exhaustive && panel_preferred(ncols, ptr[nrows], m)) {
+    if (o.priority_format == FFSPMV_FMT_AUTO && !exhaustive && o.selector != FFSPMV_SEL_LEARNED &&
+        panel_preferred(ncols, ptr[nrows], m)) {
         ffspmv_options o2 = o;
         o2.priority_format = FFSPMV_FMT_PANEL;
         return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, nullptr);
     }
-    if (o.priority_format == FFSPMV_FMT_AUTO && exhaustive && m <= 65536u && ptr[nrows] > 0) {
+    if (o.priority_format == FFSPMV_FMT_AUTO && exhaustive && ptr[nrows] > 0) {
         // the exhaustive selector also times the whole x-panel plan against
         // the binned plan of its per-bin winners and keeps the faster
         ffspmv_options ob = o;
@@ -131,6 +127,32 @@ ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
         free_plan(Q);
         P = B;
         return FFSPMV_OK;
+    }
+    if (o.priority_format == FFSPMV_FMT_AUTO && o.selector == FFSPMV_SEL_LEARNED) {
+        // the network's matrix-level outputs choose the layout: the x-panel
+        // plan, the binned plan with its own per-bin table, or the binned
+        // plan with the heuristic table (least predicted whole-plan time)
+        BinChoice bins[kBins];
+        int layout = -1;
+        ffspmv_status st = choose_bins(o.selector, nrows, ncols, ptr, col, val, m, o, bins, &layout);
+        if (st != FFSPMV_OK) return st;
+        ffspmv_options o2 = o;
+        // no network installed: the exhaustive bins, and the panel rule of AUTO
+        const bool panel = layout >= FFSPMV_LAYOUT_PANEL_Q1 || (layout < 0 && panel_preferred(ncols, ptr[nrows], m));
+        if (panel && ptr[nrows] > 0) {
+            o2.priority_format = FFSPMV_FMT_PANEL;
+            if (layout >= FFSPMV_LAYOUT_PANEL_Q1) o2.panel_cluster = 1 << (layout - FFSPMV_LAYOUT_PANEL_Q1);
+            Plan Q;
+            if (build_plan_ex(Q, nrows, ncols, ptr, col, val, m, o2, nullptr) == FFSPMV_OK && Q.panel.on) {
+                P = Q;
+                return FFSPMV_OK;
+            }
+            free_plan(Q);
+        }
+        o2.priority_format = FFSPMV_FMT_BINNED;
+        o2.panel_cluster = o.panel_cluster;
+        const bool own_table = layout != FFSPMV_LAYOUT_BINNED;
+        return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, own_table ? bins : nullptr);
     }
     const bool wants_bins = o.priority_format == FFSPMV_FMT_BINNED ||
                             (o.priority_format == FFSPMV_FMT_AUTO &&
@@ -285,39 +307,6 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
     return FFSPMV_OK;
 }
 
-// The binned plan of A (or A^T) for wide blocks on an x-panel handle, built
-// on first use from the handle's host copy of the matrix (synchronous).
-static ffspmv_status ensure_multi(ffspmv_t h, bool transpose, const Plan **out)
-{
-    Plan *&mp = h->multi[transpose ? 1 : 0];
-    if (!mp) {
-        Plan *np = new (std::nothrow) Plan();
-        if (!np) return FFSPMV_ERR_OOM;
-        ffspmv_options o = h->opt;
-        o.priority_format = FFSPMV_FMT_BINNED;
-        o.selector = FFSPMV_SEL_HEURISTIC;
-        const long long nr = h->A.nrows, nc = h->A.ncols;
-        ffspmv_status st;
-        if (!transpose) {
-            st = build_plan_ex(*np, nr, nc, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), h->m, o, nullptr);
-        } else {
-            std::vector<long long> tptr;
-            std::vector<int> tcol;
-            std::vector<u32> tval;
-            transpose_csr(nr, nc, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), tptr, tcol, tval);
-            st = build_plan_ex(*np, nc, nr, tptr.data(), tcol.data(), tval.data(), h->m, o, nullptr);
-        }
-        if (st != FFSPMV_OK) {
-            free_plan(*np);
-            delete np;
-            return st;
-        }
-        mp = np;
-    }
-    *out = mp;
-    return FFSPMV_OK;
-}
-
 static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_x,
                                   int64_t ldx, uint32_t *d_y, int64_t ldy,
                                   int32_t nvec, uint32_t alpha, uint32_t beta,
@@ -339,10 +328,6 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     if (transpose && h->transpose_mode == FFSPMV_TRANSPOSE_ATOMIC)
         return run_scatter_transpose(h, d_x, ldx, d_y, ldy, nvec, alpha % h->m, beta % h->m, st);
     const Plan *P = transpose ? &h->AT : &h->A;
-    if (P->panel.on && nvec >= kPanelMultiMin) {
-        ffspmv_status s = ensure_multi(h, transpose, &P);
-        if (s != FFSPMV_OK) return s;
-    }
     PanelCtl ctl;
     ctl.status = h->d_status + 2;
     ctl.skip_stage = (h->opt.test_hooks & 2) ? 1 : -1;
@@ -425,15 +410,7 @@ ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec, i
         const int chunk = nvec < 16 ? nvec : 16;
         n += 2LL * ((nvec + chunk - 1) / chunk);
     } else {
-        const Plan &P = transpose ? h->AT : h->A;
-        if (P.panel.on && nvec >= kPanelMultiMin) {
-            const Plan *mp = nullptr;
-            ffspmv_status s = ensure_multi(h, transpose != 0, &mp);
-            if (s != FFSPMV_OK) return s;
-            n += count_plan_launches(*mp, nvec);
-        } else {
-            n += count_plan_launches(P, nvec);
-        }
+        n += count_plan_launches(transpose ? h->AT : h->A, nvec);
     }
     *launches = n;
     return FFSPMV_OK;

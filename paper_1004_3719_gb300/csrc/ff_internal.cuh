@@ -219,10 +219,6 @@ constexpr u32 kPanelNeg = 0x8000u;            // a -1 entry (+-1 sections)
 constexpr long long kPanelLong = 32768;       // longer rows go to split CSR segments
 constexpr int kPanelSmemMax = 227 * 1024;
 constexpr int kPanelMaxPe = 32760;            // stage entries (fits the 16-bit pack counts)
-// Blocks of this many vectors or more skip the x-panel plan: a binned plan
-// reads the matrix once for all of them (Sec. 2.5.1), where the panel kernel
-// takes one pass per vector.
-constexpr int kPanelMultiMin = 3;
 static_assert(16 * kPanelStages + 4 <= kPanelDescBytes, "stage descriptors and the grid generation word");
 
 struct PanelStage {
@@ -310,9 +306,6 @@ struct ffspmv_handle {
     int *d_status = nullptr;   // device status word (timeouts)
     // patterns of the odd entries of A and A^T for the GF(2) products
     ff::Gf2Pattern *gf2[2] = {nullptr, nullptr};
-    // binned plans of A and A^T for blocks of kPanelMultiMin or more vectors
-    // when the plan is the x-panel layout (built on first use)
-    ff::Plan *multi[2] = {nullptr, nullptr};
 };
 
 namespace ff {

@@ -297,12 +297,16 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 }
 
 // Inference inputs: row b = [matrix features, features of bin b].
+// Rows 0..kBins-1: the (matrix, bin) inputs; row kBins: the matrix-level
+// input, its bin features all FFSPMV_MATRIX_INPUT.
 __global__ void k_selector_inputs(const float *__restrict__ feat, const float *__restrict__ binfeat,
                                   float *__restrict__ in)
 {
     const int b = blockIdx.x, i = threadIdx.x;
-    if (b >= kBins || i >= kIn) return;
-    in[b * kIn + i] = i < FFSPMV_NUM_FEATURES ? feat[i] : binfeat[b * FFSPMV_NUM_BIN_FEATURES + i - FFSPMV_NUM_FEATURES];
+    if (b > kBins || i >= kIn) return;
+    in[b * kIn + i] = i < FFSPMV_NUM_FEATURES ? feat[i]
+                      : b == kBins            ? FFSPMV_MATRIX_INPUT
+                                              : binfeat[b * FFSPMV_NUM_BIN_FEATURES + i - FFSPMV_NUM_FEATURES];
 }
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -533,7 +537,7 @@ ffspmv_status tune_bins(long long nrows, long long ncols, const long long *ptr, 
 }
 
 ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, const long long *hptr,
-                              const int *hcol, const u32 *hval, u32 m, int *best)
+                              const int *hcol, const u32 *hval, u32 m, int *best, int *layout)
 {
     std::vector<float> w;
     {
@@ -545,17 +549,18 @@ ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, c
     ffspmv_status rs = upload_csr(nrows, nnz, hptr, hcol, hval, d);
     if (rs != FFSPMV_OK) return rs;
     float *buf = nullptr;
+    constexpr int kRows = kBins + 1;  // the bins, then the matrix-level input
     const size_t nf = FFSPMV_MLP_PARAMS + FFSPMV_NUM_FEATURES + kBins * FFSPMV_NUM_BIN_FEATURES +
-                      kBins * kIn + kBins * 2 * kH + kBins * kOut;
+                      kRows * kIn + kRows * 2 * kH + kRows * kOut;
     if (cudaMalloc(&buf, nf * sizeof(float)) != cudaSuccess) return FFSPMV_ERR_OOM;
     float *P = buf, *feat = P + FFSPMV_MLP_PARAMS, *binf = feat + FFSPMV_NUM_FEATURES;
-    float *in = binf + kBins * FFSPMV_NUM_BIN_FEATURES, *act = in + kBins * kIn, *out = act + kBins * 2 * kH;
-    std::vector<float> hout(kBins * kOut);
+    float *in = binf + kBins * FFSPMV_NUM_BIN_FEATURES, *act = in + kRows * kIn, *out = act + kRows * 2 * kH;
+    std::vector<float> hout(kRows * kOut);
     do {
         if (cudaMemcpy(P, w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) { rs = FFSPMV_ERR_CUDA; break; }
         if ((rs = features_device(nrows, ncols, d.ptr, d.col, d.val, m, feat, binf, nullptr)) != FFSPMV_OK) break;
-        k_selector_inputs<<<kBins, 32>>>(feat, binf, in);
-        if ((rs = mlp_forward(P, in, kBins, act, out, nullptr)) != FFSPMV_OK) break;
+        k_selector_inputs<<<kRows, 32>>>(feat, binf, in);
+        if ((rs = mlp_forward(P, in, kRows, act, out, nullptr)) != FFSPMV_OK) break;
         if (cudaMemcpy(hout.data(), out, hout.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rs = FFSPMV_ERR_CUDA;
     } while (0);
     cudaFree(buf);
@@ -585,20 +590,36 @@ ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, c
             if (format_valid(f, b, maxlen[b]) && (fb < 0 || hout[b * kOut + f] < hout[b * kOut + fb])) fb = f;
         if (fb < 0) continue;
         best[3 * b] = fb;
-        best[3 * b + 1] = (pm[b] > 0 && hout[b * kOut + kFormats] < 0.f) ? 1 : 0;
+        best[3 * b + 1] = (pm[b] > 0 && hout[b * kOut + FFSPMV_OUT_PM] < 0.f) ? 1 : 0;
         best[3 * b + 2] = 1;
+    }
+    if (layout) {
+        // least predicted whole-plan time, relative to the heuristic binned plan (0)
+        const float *o = &hout[kBins * kOut];
+        *layout = FFSPMV_LAYOUT_BINNED;
+        float bestv = 0.f;
+        if (o[FFSPMV_OUT_NETBINS] < bestv) {
+            bestv = o[FFSPMV_OUT_NETBINS];
+            *layout = FFSPMV_LAYOUT_NETBINS;
+        }
+        for (int k = 0; k < 3; ++k)
+            if (o[FFSPMV_OUT_PANEL + k] < bestv) {
+                bestv = o[FFSPMV_OUT_PANEL + k];
+                *layout = FFSPMV_LAYOUT_PANEL_Q1 + k;
+            }
     }
     return FFSPMV_OK;
 }
 
 ffspmv_status choose_bins(int selector, long long nrows, long long ncols, const long long *ptr,
                           const int *col, const u32 *val, u32 m, const ffspmv_options &o,
-                          BinChoice *bins)
+                          BinChoice *bins, int *layout)
 {
     const long long nnz = ptr[nrows];
     std::vector<int> best(3 * kBins, 0);
     ffspmv_status rs = FFSPMV_ERR_UNSUPPORTED;
-    if (selector == FFSPMV_SEL_LEARNED) rs = selector_choose(nrows, ncols, nnz, ptr, col, val, m, best.data());
+    if (layout) *layout = -1;
+    if (selector == FFSPMV_SEL_LEARNED) rs = selector_choose(nrows, ncols, nnz, ptr, col, val, m, best.data(), layout);
     if (rs == FFSPMV_ERR_UNSUPPORTED || selector == FFSPMV_SEL_EXHAUSTIVE) {
         std::vector<float> t(kBins * kFormats), pt(kBins * 2);
         std::vector<long long> sn(kBins);
@@ -773,10 +794,10 @@ ffspmv_status ffspmv_heuristic_choose(int64_t nrows, const int64_t *row_ptr, con
 
 ffspmv_status ffspmv_selector_choose(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row_ptr,
                                      const int32_t *col, const uint32_t *values, uint32_t modulus,
-                                     int32_t *best)
+                                     int32_t *best, int32_t *layout)
 {
     if (nrows < 0 || ncols < 0 || nnz < 0 || !row_ptr || !best || modulus < 2u) return FFSPMV_ERR_ARG;
-    return selector_choose(nrows, ncols, nnz, (const long long *)row_ptr, col, values, modulus, best);
+    return selector_choose(nrows, ncols, nnz, (const long long *)row_ptr, col, values, modulus, best, layout);
 }
 
 }  // extern "C"

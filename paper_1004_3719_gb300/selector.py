@@ -56,16 +56,19 @@ def tune_bins(A, max_rows=16384, max_nnz=1 << 21, reps=5):
     return {"times": times, "pm_times": pm, "sample_nnz": snnz, "best": best}
 
 
-def selector_choose(A):
-    """best[17][3] from the installed selector network (inference kernel)."""
+def selector_choose(A, with_layout=False):
+    """best[17][3] from the installed selector network (inference kernel);
+    with_layout: (best, layout), layout one of LAYOUT_BINNED (heuristic
+    table), LAYOUT_NETBINS (binned, the network's table) or LAYOUT_PANEL."""
     best = np.zeros((NUM_BINS, 3), dtype=np.int32)
+    layout = np.zeros(1, dtype=np.int32)
     rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(A.col, dtype=np.int32)
     vl = np.ascontiguousarray(A.val, dtype=np.uint32)
     check(lib().ffspmv_selector_choose(A.nrows, A.ncols, int(rp[-1]), _ptr(rp), _ptr(cl),
-                                       _ptr(vl), int(A.modulus), _ptr(best)),
+                                       _ptr(vl), int(A.modulus), _ptr(best), _ptr(layout)),
           "ffspmv_selector_choose")
-    return best
+    return (best, int(layout[0])) if with_layout else best
 
 
 def heuristic_choose(A, use_pm1=-1):

@@ -8,15 +8,22 @@
    moduli 3, 65521, 2^31-1), made by worker processes (spawn) while the GPU
    works.  For every matrix: the device features, then the exhaustive search
    (every valid format of every non-empty bin timed on a row sample).
-2. Training samples are the (matrix, bin) pairs: input = 16 matrix features +
+2. Whole-plan timings of every matrix: y = A x with the binned plan of the
+   heuristic table (t_H), the binned plan of the exhaustive search's table
+   (t_E) and the x-panel plan (t_P), L2 flushed before each call.
+3. Training samples are the (matrix, bin) pairs: input = 16 matrix features +
    6 bin features; target = log(t_format / t_best) for each valid format and
-   log(t_pm / t_nopm) for the +-1 flag.  The network is trained on the GPU by
-   the library's own forward / loss / backward / Adam kernels.
-3. Evaluation on the held-out matrices: the cost of a choice is the sum over
-   bins of (sample time per entry) x (entries of the bin); the report gives
-   exhaustive-best cost / chosen cost ("% of exhaustive-best throughput") for
-   the network, the heuristic table and a single fixed CSR width, and a few
-   whole-matrix timings of the resulting plans.
+   log(t_pm / t_nopm) for the +-1 flag; and one matrix-level sample per
+   matrix: the 16 features with every bin feature set to MATRIX_INPUT,
+   target = log(t_P / t_H) and log(t_E / t_H).  The network is trained on the
+   GPU by the library's own forward / loss / backward / Adam kernels.
+4. Evaluation on the held-out matrices: (a) per bin, the cost of a choice is
+   the sum over bins of (sample time per entry) x (entries of the bin); the
+   report gives exhaustive-best cost / chosen cost ("% of exhaustive-best
+   throughput") for the network, the heuristic table and a single fixed CSR
+   width; (b) whole plan, the best of t_H, t_E, t_P over the time of the
+   layout each chooser picks; (c) whole-matrix timings of the handles that
+   FMT.AUTO builds under each selector.
 """
 from __future__ import annotations
 
@@ -24,6 +31,7 @@ import argparse
 import json
 import multiprocessing as mp
 import os
+import re
 import sys
 import time
 
@@ -34,7 +42,15 @@ ROOT = os.path.dirname(HERE)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-NUM_BINS, NUM_FORMATS = 17, 10
+from paper_1004_3719_gb300._lib import (LAYOUT_BINNED, LAYOUT_NETBINS,  # noqa: E402
+                                       LAYOUT_PANEL_Q1, LAYOUT_PANEL_Q2, LAYOUT_PANEL_Q4,
+                                       MATRIX_INPUT, MLP_OUT, NUM_BIN_FEATURES, NUM_BINS,
+                                       NUM_FORMATS, OUT_NETBINS, OUT_PANEL, OUT_PM)
+
+# whole-plan timing keys: binned with the heuristic table (H) and with the
+# exhaustive table (E), x-panel with clusters of 1, 2 and 4 CTAs (P1, P2, P4)
+LAYOUT_KEY = {LAYOUT_BINNED: "H", LAYOUT_NETBINS: "E", LAYOUT_PANEL_Q1: "P1",
+              LAYOUT_PANEL_Q2: "P2", LAYOUT_PANEL_Q4: "P4"}
 
 
 def _make(args):
@@ -45,7 +61,7 @@ def _make(args):
 
 
 def samples_of(feat, binfeat, tune, min_sample_nnz=256):
-    """Training rows of one matrix: (x[k][22], target[k][11], mask[k][11], bins)."""
+    """Training rows of one matrix's bins: (x[k][22], target[k][13], mask[k][13], bins)."""
     X, T, Mk, bins = [], [], [], []
     t = tune["times"].astype(np.float64)
     pm = tune["pm_times"].astype(np.float64)
@@ -55,18 +71,103 @@ def samples_of(feat, binfeat, tune, min_sample_nnz=256):
         tb = t[b]
         ok = np.isfinite(tb) & (tb > 0)
         best = tb[ok].min()
-        target = np.zeros(NUM_FORMATS + 1)
-        mask = np.zeros(NUM_FORMATS + 1)
+        target = np.zeros(MLP_OUT)
+        mask = np.zeros(MLP_OUT)
         target[:NUM_FORMATS][ok] = np.log(tb[ok] / best)
         mask[:NUM_FORMATS][ok] = 1.0
         if np.isfinite(pm[b, 1]) and pm[b, 0] > 0 and pm[b, 1] > 0:
-            target[NUM_FORMATS] = np.log(pm[b, 1] / pm[b, 0])
-            mask[NUM_FORMATS] = 1.0
+            target[OUT_PM] = np.log(pm[b, 1] / pm[b, 0])
+            mask[OUT_PM] = 1.0
         X.append(np.concatenate([feat, binfeat[b]]))
         T.append(target)
         Mk.append(mask)
         bins.append(b)
     return X, T, Mk, bins
+
+
+def matrix_sample(feat, plan_us):
+    """The matrix-level training row: (x[22], target[13], mask[13]), or None
+    when the heuristic binned plan was not timed."""
+    tH = plan_us.get("H", np.nan)
+    if not (np.isfinite(tH) and tH > 0):
+        return None
+    x = np.concatenate([feat, np.full(NUM_BIN_FEATURES, MATRIX_INPUT)])
+    target = np.zeros(MLP_OUT)
+    mask = np.zeros(MLP_OUT)
+    outs = [(OUT_NETBINS, "E")] + [(OUT_PANEL + i, f"P{q}") for i, q in enumerate((1, 2, 4))]
+    for k, t in ((k, plan_us.get(key, np.nan)) for k, key in outs):
+        if np.isfinite(t) and t > 0:
+            target[k] = np.log(t / tH)
+            mask[k] = 1.0
+    return x, target, mask
+
+
+def panel_rule(A):
+    """The layout FMT.AUTO takes under the heuristic selector (the rule of
+    panel_preferred in csrc/api.cu): x-panel when m <= 2^16, nnz >= 2^21 and
+    nnz >= 3 ncols."""
+    return A.modulus <= 65536 and A.nnz >= (1 << 21) and A.nnz >= 3 * A.ncols
+
+
+def time_handle(ff, M, x, y, flush, reps=7):
+    """Median microseconds of one y = A x on handle M, L2 flushed before each
+    call (3 untimed calls first)."""
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, st.cuda_stream)
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, st.cuda_stream)
+        e1.record(st)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return 1e3 * float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+
+def whole_plan_times(ff, sel, A, tune, heur, flush):
+    """Whole-plan microseconds of one matrix (NaN: not buildable): H, E,
+    P1, P2, P4, and P = the x-panel plan with the builder's own cluster size
+    ("q" holds that size)."""
+    import torch
+    x = torch.zeros(max(A.ncols, 1), dtype=torch.int32, device="cuda")
+    y = torch.empty(max(A.nrows, 1), dtype=torch.int32, device="cuda")
+    out = {}
+    makers = {"H": lambda: sel.create_binned(A, heur, transpose_mode=2),
+              "E": lambda: sel.create_binned(A, tune["best"], transpose_mode=2),
+              "P": lambda: ff.Matrix.from_csr(A, priority_format=ff.FMT.PANEL, transpose_mode=2)}
+    for q in (1, 2, 4):
+        makers[f"P{q}"] = (lambda q=q: ff.Matrix.from_csr(A, priority_format=ff.FMT.PANEL, panel_cluster=q,
+                                                          transpose_mode=2))
+    out["q"] = 0
+    for k, make in makers.items():
+        if k.startswith("P") and k != "P" and k == f"P{out['q']}":
+            out[k] = out["P"]  # the builder's own choice, timed already
+            continue
+        try:
+            M = make()
+        except ff.FFSPMVError:
+            out[k] = np.nan
+            continue
+        d = M.describe()
+        if k.startswith("P") and "panels" not in d:
+            out[k] = np.nan
+        else:
+            out[k] = time_handle(ff, M, x, y, flush)
+            if k == "P":
+                mq = re.search(r"x (\d+) column groups", d)
+                out["q"] = int(mq.group(1)) if mq else 0
+        M.close()
+    return out
+
+
+def layout_time(plan_us, layout):
+    t = plan_us.get(LAYOUT_KEY[layout], np.nan)
+    return t if np.isfinite(t) else plan_us["H"]
 
 
 def choice_cost(tune, nnz_b, best):
@@ -143,6 +244,8 @@ def main():
     ap.add_argument("--corpus", default="", help="npz cache of the corpus (read if present)")
     ap.add_argument("--report", default="")
     ap.add_argument("--e2e", type=int, default=6, help="held-out matrices timed end to end")
+    ap.add_argument("--matrix-weight", type=int, default=4,
+                    help="copies of each matrix-level sample in the training set")
     args = ap.parse_args()
 
     ctx = mp.get_context("spawn")
@@ -159,6 +262,7 @@ def main():
         data = dict(np.load(args.corpus, allow_pickle=True))
     t0 = time.time()
     recs = []
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if data is None:
         jobs = [(args.seed, i, args.rows_lo, args.rows_hi) for i in range(n_all)]
         for k, (i, A) in enumerate(pool.imap(_make, jobs, chunksize=1)):
@@ -167,7 +271,8 @@ def main():
             heur = sel.heuristic_choose(A)
             recs.append(dict(index=i, name=A.name, nrows=A.nrows, nnz=A.nnz, feat=feat,
                              binfeat=binfeat, tune=tune, heur=heur, fixed=fixed_csr_choice(A),
-                             nnz_b=bin_nnz(A)))
+                             nnz_b=bin_nnz(A), plan_us=whole_plan_times(ff, sel, A, tune, heur, flush),
+                             panel_rule=panel_rule(A)))
             if (k + 1) % 50 == 0:
                 print(f"[corpus] {k + 1}/{n_all} matrices, {time.time() - t0:.0f} s", flush=True)
         if args.corpus:
@@ -186,6 +291,11 @@ def main():
             X += x
             T += t
             Mk += mk
+            ms = matrix_sample(r["feat"], r["plan_us"])
+            if ms is not None:
+                X += [ms[0]] * args.matrix_weight
+                T += [ms[1]] * args.matrix_weight
+                Mk += [ms[2]] * args.matrix_weight
         return (np.array(X, dtype=np.float32), np.array(T, dtype=np.float32),
                 np.array(Mk, dtype=np.float32))
 
@@ -210,33 +320,51 @@ def main():
     sel.selector_load(params)
 
     # held-out evaluation
-    rows = []
+    rows, whole = [], []
     for r in test_recs:
         best_c = best_cost(r["tune"], r["nnz_b"])
-        learned = learned_choice(net, r)
+        learned, layout = learned_choice(net, r)
         rows.append(dict(name=r["name"], nrows=r["nrows"], nnz=r["nnz"],
                          learned=best_c / choice_cost(r["tune"], r["nnz_b"], learned),
                          heuristic=best_c / choice_cost(r["tune"], r["nnz_b"], r["heur"]),
                          fixed_csr=best_c / choice_cost(r["tune"], r["nnz_b"], r["fixed"])))
+        pu = r["plan_us"]
+        if np.isfinite(pu.get("H", np.nan)):
+            tb = np.nanmin([pu.get(k, np.nan) for k in ("H", "E", "P", "P1", "P2", "P4")])
+            t_heur = pu["P"] if r["panel_rule"] and np.isfinite(pu.get("P", np.nan)) else pu["H"]
+            t_exh = np.nanmin([pu.get("E", np.nan), pu.get("P", np.nan), np.inf])
+            whole.append(dict(name=r["name"], layout=layout, learned=tb / layout_time(pu, layout),
+                              heuristic=tb / t_heur, exhaustive=tb / (t_exh if np.isfinite(t_exh) else pu["H"]),
+                              learned_us=layout_time(pu, layout), heuristic_us=t_heur))
     summ = {k: dict(mean=float(np.mean([x[k] for x in rows])), median=float(np.median([x[k] for x in rows])),
                     min=float(np.min([x[k] for x in rows])))
             for k in ("learned", "heuristic", "fixed_csr")}
+    summ_whole = {k: dict(mean=float(np.mean([x[k] for x in whole])), median=float(np.median([x[k] for x in whole])),
+                          min=float(np.min([x[k] for x in whole])))
+                  for k in ("learned", "heuristic", "exhaustive")} if whole else {}
+    layouts = {n: int(sum(1 for w in whole if w["layout"] == v))
+               for n, v in (("binned", LAYOUT_BINNED), ("netbins", LAYOUT_NETBINS), ("panel_q1", LAYOUT_PANEL_Q1),
+                            ("panel_q2", LAYOUT_PANEL_Q2), ("panel_q4", LAYOUT_PANEL_Q4))}
+    total_us = {k: float(sum(w[k + "_us"] for w in whole)) for k in ("learned", "heuristic")}
     e2e = end_to_end(ff, sel, test_recs[:args.e2e], args) if args.e2e > 0 else []
     result = dict(train_matrices=len(train_recs), test_matrices=len(test_recs),
                   train_samples=int(Xtr.shape[0]), corpus_seconds=round(t_corpus, 1),
-                  train_seconds=round(t_train, 1), losses=losses, summary=summ, e2e=e2e)
+                  train_seconds=round(t_train, 1), losses=losses, summary=summ,
+                  whole_plan=summ_whole, layouts=layouts, total_us=total_us, e2e=e2e)
     print(json.dumps(result))
     if args.report:
         write_report(args, result, rows)
 
 
 def learned_choice(net, r):
-    """The network's choice for a corpus record (same rule as the library's
-    inference: argmin over valid formats, +-1 when the predicted log ratio < 0)."""
+    """The network's choice for a corpus record, by the library's inference
+    rule: per bin the argmin over valid formats and +-1 when the predicted log
+    ratio is negative; the layout of least predicted whole-plan time (the
+    heuristic binned plan counting 0).  Returns (best[17][3], layout)."""
     import torch
-    X = np.array([np.concatenate([r["feat"], r["binfeat"][b]]) for b in range(NUM_BINS)],
-                 dtype=np.float32)
-    out, _ = net.forward(torch.from_numpy(X).to(net.dev))
+    X = [np.concatenate([r["feat"], r["binfeat"][b]]) for b in range(NUM_BINS)]
+    X.append(np.concatenate([r["feat"], np.full(NUM_BIN_FEATURES, MATRIX_INPUT)]))
+    out, _ = net.forward(torch.from_numpy(np.array(X, dtype=np.float32)).to(net.dev))
     out = out.cpu().numpy()
     t = r["tune"]["times"]
     best = np.zeros((NUM_BINS, 3), dtype=np.int32)
@@ -245,45 +373,39 @@ def learned_choice(net, r):
         if not valid.any():
             continue
         scores = np.where(valid, out[b, :NUM_FORMATS], np.inf)
-        best[b] = [int(np.argmin(scores)), int(out[b, NUM_FORMATS] < 0), 1]
-    return best
+        best[b] = [int(np.argmin(scores)), int(out[b, OUT_PM] < 0), 1]
+    layout, v = LAYOUT_BINNED, 0.0
+    if out[NUM_BINS, OUT_NETBINS] < v:
+        layout, v = LAYOUT_NETBINS, out[NUM_BINS, OUT_NETBINS]
+    for i, lay in enumerate((LAYOUT_PANEL_Q1, LAYOUT_PANEL_Q2, LAYOUT_PANEL_Q4)):
+        if out[NUM_BINS, OUT_PANEL + i] < v:
+            layout, v = lay, out[NUM_BINS, OUT_PANEL + i]
+    return best, layout
 
 
 def end_to_end(ff, sel, recs, args):
-    """Whole-matrix y = A x timings (L2 flushed between calls) of the plans
-    from the network, the exhaustive search, the heuristic table and the
-    plain fixed-width CSR format."""
+    """Whole-matrix y = A x timings (L2 flushed between calls) of the handles
+    FMT.AUTO builds under the learned, exhaustive and heuristic selectors,
+    and of the plain fixed-width CSR format."""
     import torch
 
     import gen
     out = []
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    sink = torch.zeros(64 << 20, dtype=torch.int32, device="cuda")
-    st = torch.cuda.current_stream()
     for r in recs:
         A = gen.selector_matrix(args.seed, r["index"], rows_lo=args.rows_lo, rows_hi=args.rows_hi)
         x = torch.from_numpy(gen.uniform_block(7, A.ncols, 1, A.modulus).view(np.int32)).cuda()
         y = torch.empty(A.nrows, dtype=torch.int32, device="cuda")
         res = {"name": A.name, "nnz": A.nnz}
-        plans = {"learned": sel.create_binned(A, sel.selector_choose(A), transpose_mode=2),
-                 "exhaustive": sel.create_binned(A, r["tune"]["best"], transpose_mode=2),
-                 "heuristic": sel.create_binned(A, r["heur"], transpose_mode=2),
-                 "fixed_csr": ff.Matrix.from_csr(A, priority_format=ff.FMT.CSR, transpose_mode=2)}
-        for k, M in plans.items():
-            for _ in range(3):
-                ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, st.cuda_stream)
-            ts = []
-            for _ in range(10):
-                flush.fill_(1)
-                s_ = sink.sum()  # noqa: F841
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                ff.spmv_apply(M.handle, x, 1, y, 1, 1, 1, 0, st.cuda_stream)
-                e1.record(st)
-                ts.append((e0, e1))
-            torch.cuda.synchronize()
-            res[k + "_us"] = round(1e3 * float(np.median([a.elapsed_time(b) for a, b in ts])), 1)
+        makers = {"learned": lambda: ff.Matrix.from_csr(A, selector=ff.SEL.LEARNED, transpose_mode=2),
+                  "exhaustive": lambda: ff.Matrix.from_csr(A, selector=ff.SEL.EXHAUSTIVE, transpose_mode=2),
+                  "heuristic": lambda: ff.Matrix.from_csr(A, transpose_mode=2),
+                  "fixed_csr": lambda: ff.Matrix.from_csr(A, priority_format=ff.FMT.CSR, transpose_mode=2)}
+        for k, make in makers.items():
+            M = make()
+            res[k + "_us"] = round(time_handle(ff, M, x, y, flush, reps=10), 1)
+            res[k + "_layout"] = "panel" if "panels" in M.describe() else "binned"
+            M.close()
         out.append(res)
     return out
 
@@ -294,7 +416,8 @@ def write_report(args, result, rows):
         "# Format selector: training and held-out evaluation",
         "",
         f"Command: `python -m paper_1004_3719_gb300.train_selector --train {args.train} --test {args.test} "
-        f"--seed {args.seed} --steps {args.steps}` (one GB300).",
+        f"--seed {args.seed} --steps {args.steps} --matrix-weight {args.matrix_weight} --e2e {args.e2e}` "
+        "(one GB300).",
         "",
         f"* corpus: {result['train_matrices']} training + {result['test_matrices']} held-out matrices, "
         f"{result['train_samples']} (matrix, bin) training samples; corpus {result['corpus_seconds']} s, "
@@ -309,12 +432,27 @@ def write_report(args, result, rows):
     ]
     for k in ("learned", "heuristic", "fixed_csr"):
         lines.append(f"| {k} | {100 * s[k]['mean']:.1f}% | {100 * s[k]['median']:.1f}% | {100 * s[k]['min']:.1f}% |")
+    w = result["whole_plan"]
+    if w:
+        lines += ["", "Held-out whole-plan layout choice: best of (binned with the heuristic table, binned with "
+                  "the exhaustive table, x-panel) over the time of the layout each chooser picks "
+                  "(learned: the network's matrix-level outputs; heuristic: the AUTO panel rule; exhaustive: the "
+                  "faster of its binned plan and the x-panel plan):", "",
+                  "| chooser | mean | median | min |", "|---|---|---|---|"]
+        for k in ("learned", "heuristic", "exhaustive"):
+            lines.append(f"| {k} | {100 * w[k]['mean']:.1f}% | {100 * w[k]['median']:.1f}% | "
+                         f"{100 * w[k]['min']:.1f}% |")
+        t = result["total_us"]
+        lines += ["", f"Layouts the network picked: {result['layouts']}; summed held-out time "
+                  f"{t['learned']:.0f} µs (learned) vs {t['heuristic']:.0f} µs (heuristic AUTO)."]
     if result["e2e"]:
-        lines += ["", "Whole-matrix y = A x (µs, median of 10, L2 flushed):", "",
+        lines += ["", "Whole-matrix y = A x of the FMT.AUTO handles per selector (µs, median of 10, L2 flushed; "
+                  "layout in brackets):", "",
                   "| matrix | nnz | learned | exhaustive | heuristic | fixed CSR |", "|---|---|---|---|---|---|"]
         for e in result["e2e"]:
-            lines.append(f"| {e['name']} | {e['nnz']} | {e['learned_us']} | {e['exhaustive_us']} | "
-                         f"{e['heuristic_us']} | {e['fixed_csr_us']} |")
+            lines.append(f"| {e['name']} | {e['nnz']} | {e['learned_us']} ({e['learned_layout']}) | "
+                         f"{e['exhaustive_us']} ({e['exhaustive_layout']}) | "
+                         f"{e['heuristic_us']} ({e['heuristic_layout']}) | {e['fixed_csr_us']} |")
     with open(args.report, "w") as f:
         f.write("\n".join(lines) + "\n")
 

@@ -125,22 +125,31 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 
 
 @pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained selector weights committed")
-def test_learned_selector_exact_and_better_than_heuristic(lib):
-    """Held-out matrices (indices beyond the training corpus): the learned
-    plans are bit-exact, and under the exhaustive search's own timings their
-    cost is no worse than the heuristic table's on average."""
-    from paper_1004_3719_gb300 import selector as sel
-    from paper_1004_3719_gb300.train_selector import best_cost, bin_nnz, choice_cost
-    ratios_l, ratios_h = [], []
-    for idx in range(50_000, 50_006):
-        A = gen.selector_matrix(1005, idx, rows_hi=200_000)
-        learned = sel.selector_choose(A)
-        M = lib.Matrix.from_csr(A, selector=lib.SEL.LEARNED, transpose_mode=lib.TRANSPOSE.NONE)
+def test_learned_selector_exact_and_faster_than_heuristic(lib):
+    """Held-out matrices (indices beyond the training corpus, 10^4 to 2*10^6
+    rows): FMT.AUTO under the learned selector gives bit-exact products, and
+    its summed measured time of y = A x (CUDA events, L2 flushed before each
+    call, median of 9) is below that of FMT.AUTO under the heuristic
+    selector, the same handles a user gets."""
+    import torch
+
+    from paper_1004_3719_gb300.train_selector import time_handle
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    t_l = t_h = 0.0
+    per = []
+    for idx in range(50_000, 50_010):
+        A = gen.selector_matrix(1005, idx, rows_lo=10_000, rows_hi=2_000_000)
         x = rand_block(idx, A.ncols, 1, A.modulus)
-        assert np.array_equal(to_host(M.apply(to_dev(x))), oracle.csr_spmv(A, x)), A.name
-        tune = sel.tune_bins(A)
-        nb = bin_nnz(A)
-        b = best_cost(tune, nb)
-        ratios_l.append(b / choice_cost(tune, nb, learned))
-        ratios_h.append(b / choice_cost(tune, nb, sel.heuristic_choose(A)))
-    assert np.mean(ratios_l) >= np.mean(ratios_h) - 0.02, (ratios_l, ratios_h)
+        xd = to_dev(x)
+        y = torch.empty(A.nrows, dtype=torch.int32, device="cuda")
+        ML = lib.Matrix.from_csr(A, selector=lib.SEL.LEARNED, transpose_mode=lib.TRANSPOSE.NONE)
+        assert np.array_equal(to_host(ML.apply(xd)), oracle.csr_spmv(A, x)), A.name
+        tl = time_handle(lib, ML, xd, y, flush, reps=9)
+        ML.close()
+        MH = lib.Matrix.from_csr(A, transpose_mode=lib.TRANSPOSE.NONE)
+        th = time_handle(lib, MH, xd, y, flush, reps=9)
+        MH.close()
+        t_l += tl
+        t_h += th
+        per.append((A.name, round(tl, 1), round(th, 1)))
+    assert t_l < t_h, (t_l, t_h, per)

@@ -11,10 +11,10 @@ from oracle import mlp
 
 def test_mlp_gradient_matches_finite_differences():
     rng = np.random.default_rng(0)
-    p = rng.normal(0, 0.3, 64 * 22 + 64 + 64 * 64 + 64 + 11 * 64 + 11)
-    x = rng.normal(0, 1, (7, 22))
-    t = rng.normal(0, 1, (7, 11))
-    mask = (rng.random((7, 11)) < 0.7).astype(float)
+    p = rng.normal(0, 0.3, mlp.H * mlp.IN + mlp.H + mlp.H * mlp.H + mlp.H + mlp.OUT * mlp.H + mlp.OUT)
+    x = rng.normal(0, 1, (7, mlp.IN))
+    t = rng.normal(0, 1, (7, mlp.OUT))
+    mask = (rng.random((7, mlp.OUT)) < 0.7).astype(float)
     out, cache = mlp.forward(p, x)
     L0, dout = mlp.loss(out, t, mask)
     g = mlp.backward(p, cache, dout)
@@ -29,12 +29,12 @@ def test_mlp_gradient_matches_finite_differences():
 def test_mlp_forward_hand_computed():
     # one path: x[5] -(W1[3][5]=2)-> h1[3] -(W2[7][3]=-0.5, b2[7]=4)-> h2[7] -(W3[2][7]=3)-> out[2]
     W1, b1, W2, b2, W3, b3 = (np.zeros((64, 22)), np.zeros(64), np.zeros((64, 64)),
-                              np.zeros(64), np.zeros((11, 64)), np.zeros(11))
+                              np.zeros(64), np.zeros((mlp.OUT, 64)), np.zeros(mlp.OUT))
     W1[3, 5] = 2.0
     W2[7, 3] = -0.5
     b2[7] = 4.0
     W3[2, 7] = 3.0
-    b3[:] = np.arange(11)
+    b3[:] = np.arange(mlp.OUT)
     p = mlp.pack([W1, b1, W2, b2, W3, b3])
     x = np.zeros((3, 22))
     x[0, 5] = 1.0    # h1 = 2, h2 = relu(-1 + 4) = 3, out[2] = 9 + 2
@@ -42,8 +42,8 @@ def test_mlp_forward_hand_computed():
     x[2, 5] = 10.0   # h1 = 20, h2 = relu(-10 + 4) = 0, out[2] = 0 + 2
     out, _ = mlp.forward(p, x)
     assert np.allclose(out[:, 2], [11.0, 14.0, 2.0])
-    others = [k for k in range(11) if k != 2]
-    assert np.allclose(out[:, others], np.arange(11)[others])
+    others = [k for k in range(mlp.OUT) if k != 2]
+    assert np.allclose(out[:, others], np.arange(mlp.OUT)[others])
 
 
 def test_adam_first_step_is_lr_sign():
