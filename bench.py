@@ -331,9 +331,9 @@ def extra_formats(torch, ff, flush, stream, moduli=(65521, 2**31 - 1, 3)):
 
 def extra_multivec(torch, ff, flush, stream):
     """Y = A X on the 1M power-law matrix (m = 65521) for blocks of 1 to 16
-    vectors through AUTO: one vector runs the x-panel kernel; from three
-    vectors on, a binned plan reads the matrix once for the whole block
-    (Sec. 2.5.1), next to the time of that many single-vector products."""
+    vectors through AUTO (the x-panel layout): passes of 4 or 2 vectors read
+    the matrix once for all of them (Sec. 2.5.1), next to the time of that
+    many single-vector products."""
     sp = stream.cuda_stream
     m = 65521
     A = gen.powerlaw_matrix(seed=SEED, m=m)

@@ -128,11 +128,12 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
  * beta y and its block form).  d_x: ncols x nvec (ldx), d_y: nrows x nvec
  * (ldy); 1 <= nvec; alpha, beta < m (reduced if not).  beta = 0 never reads
  * d_y ("apply": y <- A x).  d_x and d_y must not overlap.  On a handle whose
- * plan is the x-panel layout, a block runs one panel pass per vector (a
- * binned plan that reads the matrix once per block measured 2.5 to 3 times
- * slower per vector on the 1M x 1M power-law matrix).  Calls on one handle
- * must not overlap on the GPU (the x-panel plan stages x in a buffer of the
- * handle).
+ * plan is the x-panel layout, a block runs in passes of 4 vectors (m <=
+ * 2^16) or 2, then 1: each pass reads the matrix once for all its vectors
+ * (Sec. 2.5.1) on an x-panel layout built for that width; the first block
+ * that needs a width builds its layout (synchronous, host work plus one
+ * allocation per handle, direction and width).  Calls on one handle must not
+ * overlap on the GPU (the x-panel plans stage x in buffers of the handle).
  */
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx,
                          uint32_t *d_y, int64_t ldy, int32_t nvec,
@@ -232,7 +233,8 @@ ffspmv_status spmv_describe_plan(ffspmv_t h, char *buf, size_t len);
 
 /* Number of kernel launches that one spmv_apply (transpose = 0) or
  * spmv_apply_transpose (transpose = 1) call with nvec vectors enqueues
- * (host arithmetic only, nothing is enqueued). */
+ * (nothing is enqueued; on an x-panel handle this builds the layouts for
+ * the pass widths the block needs, as spmv_apply does). */
 ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec,
                                   int64_t *launches);
 
@@ -272,7 +274,9 @@ ffspmv_status spmv_check_status(ffspmv_t h, ffspmv_stream_t stream);
  * Testing aid for the x-panel layout (FFSPMV_FMT_PANEL); the paper has no
  * counterpart.  Runs only the host half of the layout for the CSR matrix
  * (row_ptr, col, values as in spmv_create_hybrid, host memory) with q CTAs
- * per cluster (1, 2 or 4) and `clusters` resident clusters, then decodes
+ * per cluster (1, 2 or 4), `clusters` resident clusters and nv vectors per
+ * pass (1, 2, or 4 when m <= 2^16: the geometry of the layout that a block
+ * of that many vectors runs on), then decodes
  * every stored entry back to (row, column, value) and writes the first `cap`
  * of them to out_row / out_col / out_val (host arrays); *out_n = the number
  * decoded.  Padding (value 0) is skipped, so are explicit zeros; rows longer
@@ -288,8 +292,8 @@ ffspmv_status spmv_check_status(ffspmv_t h, ffspmv_stream_t stream);
  */
 ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const int64_t *row_ptr,
                                   const int32_t *col, const uint32_t *values, uint32_t m,
-                                  int32_t use_pm1, int32_t q, int32_t clusters, int64_t cap,
-                                  int64_t *out_row, int64_t *out_col, uint32_t *out_val,
+                                  int32_t use_pm1, int32_t q, int32_t nv, int32_t clusters,
+                                  int64_t cap, int64_t *out_row, int64_t *out_col, uint32_t *out_val,
                                   int64_t *out_n, double *stats);
 
 #ifdef __cplusplus

@@ -79,7 +79,7 @@ def _declare(L):
     L.spmv_apply_transpose_noalloc.restype = ctypes.c_int
     L.spmv_count_launches.argtypes = [_P, _I32, _I32, ctypes.POINTER(_I64)]
     L.spmv_count_launches.restype = ctypes.c_int
-    L.ffspmv_panel_decode.argtypes = [_I64, _I64, _P, _P, _P, _U32, _I32, _I32, _I32, _I64, _P, _P, _P,
+    L.ffspmv_panel_decode.argtypes = [_I64, _I64, _P, _P, _P, _U32, _I32, _I32, _I32, _I32, _I64, _P, _P, _P,
                                       ctypes.POINTER(_I64), _P]
     L.ffspmv_panel_decode.restype = ctypes.c_int
     L.spmv_check_status.argtypes = [_P, _P]

@@ -45,6 +45,12 @@ void destroy_handle(ffspmv_handle *h)
     if (!h) return;
     free_plan(h->A);
     free_plan(h->AT);
+    for (auto &dir : h->multi)
+        for (ff::Plan *&mp : dir) {
+            if (mp) free_plan(*mp);
+            delete mp;
+            mp = nullptr;
+        }
     if (h->scatter) cudaFree(h->scatter);
     if (h->csr_arena) cudaFree(h->csr_arena);
     if (h->d_status) cudaFree(h->d_status);
@@ -307,6 +313,52 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
     return FFSPMV_OK;
 }
 
+// The x-panel plan of A (or A^T) for nv = 2 or 4 vectors per pass, built on
+// first use from the handle's host copy of the matrix (synchronous).  *out is
+// null when that layout does not exist for the matrix (the caller then runs
+// one vector per pass).
+static ffspmv_status ensure_multi(ffspmv_t h, bool transpose, int nv, const Plan **out)
+{
+    Plan *&mp = h->multi[transpose ? 1 : 0][nv == 4 ? 1 : 0];
+    if (!mp) {
+        Plan *np = new (std::nothrow) Plan();
+        if (!np) return FFSPMV_ERR_OOM;
+        ffspmv_options o = h->opt;
+        o.priority_format = FFSPMV_FMT_PANEL;
+        o.panel_cluster = (transpose ? h->AT : h->A).panel.q;
+        const long long nr = h->A.nrows, nc = h->A.ncols;
+        ffspmv_status st;
+        if (!transpose) {
+            st = build_plan_ex(*np, nr, nc, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), h->m, o, nullptr, nv);
+        } else {
+            std::vector<long long> tptr;
+            std::vector<int> tcol;
+            std::vector<u32> tval;
+            transpose_csr(nr, nc, h->h_ptr.data(), h->h_col.data(), h->h_val.data(), tptr, tcol, tval);
+            st = build_plan_ex(*np, nc, nr, tptr.data(), tcol.data(), tval.data(), h->m, o, nullptr, nv);
+        }
+        if (st != FFSPMV_OK && st != FFSPMV_ERR_UNSUPPORTED) {
+            free_plan(*np);
+            delete np;
+            return st;
+        }
+        if (st != FFSPMV_OK) {
+            free_plan(*np);
+            *np = Plan();  // no such layout: remembered as a plan without panels
+        }
+        mp = np;
+    }
+    *out = (mp->panel.on && mp->panel.nv == nv) ? mp : nullptr;
+    return FFSPMV_OK;
+}
+
+// Vectors in the next pass over a block with `left` vectors still to go.
+static int pass_width(const Plan &P, int left)
+{
+    if (left >= 4 && P.panel.small) return 4;
+    return left >= 2 ? 2 : 1;
+}
+
 static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_x,
                                   int64_t ldx, uint32_t *d_y, int64_t ldy,
                                   int32_t nvec, uint32_t alpha, uint32_t beta,
@@ -331,7 +383,26 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     PanelCtl ctl;
     ctl.status = h->d_status + 2;
     ctl.skip_stage = (h->opt.test_hooks & 2) ? 1 : -1;
-    return run_plan(*P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, &ctl);
+    if (!P->panel.on || nvec == 1)
+        return run_plan(*P, d_x, ldx, d_y, ldy, nvec, h->m, alpha % h->m, beta % h->m, st, &ctl);
+    // x-panel blocks: passes of 4 or 2 vectors read the matrix once for all
+    // of them (Sec. 2.5.1), on layouts built for that width
+    for (int c0 = 0; c0 < nvec;) {
+        int nv = pass_width(*P, nvec - c0);
+        const Plan *Q = P;
+        if (nv > 1) {
+            ffspmv_status s = ensure_multi(h, transpose, nv, &Q);
+            if (s != FFSPMV_OK) return s;
+            if (!Q) {
+                Q = P;
+                nv = 1;
+            }
+        }
+        ffspmv_status s = run_plan(*Q, d_x + c0, ldx, d_y + c0, ldy, nv, h->m, alpha % h->m, beta % h->m, st, &ctl);
+        if (s != FFSPMV_OK) return s;
+        c0 += nv;
+    }
+    return FFSPMV_OK;
 }
 
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx, uint32_t *d_y,
@@ -410,7 +481,25 @@ ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec, i
         const int chunk = nvec < 16 ? nvec : 16;
         n += 2LL * ((nvec + chunk - 1) / chunk);
     } else {
-        n += count_plan_launches(transpose ? h->AT : h->A, nvec);
+        const Plan &P = transpose ? h->AT : h->A;
+        if (!P.panel.on || nvec == 1) {
+            n += count_plan_launches(P, nvec);
+        } else {
+            for (int c0 = 0; c0 < nvec;) {
+                int nv = pass_width(P, nvec - c0);
+                const Plan *Q = &P;
+                if (nv > 1) {
+                    ffspmv_status s = ensure_multi(h, transpose != 0, nv, &Q);
+                    if (s != FFSPMV_OK) return s;
+                    if (!Q) {
+                        Q = &P;
+                        nv = 1;
+                    }
+                }
+                n += count_plan_launches(*Q, nv);
+                c0 += nv;
+            }
+        }
     }
     *launches = n;
     return FFSPMV_OK;

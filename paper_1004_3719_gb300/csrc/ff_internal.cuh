@@ -235,6 +235,7 @@ struct PanelStage {
 struct PanelPart {
     bool on = false;
     bool small = true;   // m <= 2^16: u16 x and values, u32 row sums
+    int nv = 1;          // vectors per pass: x and row sums interleaved by vector
     int q = 1;           // CTAs per cluster (column groups)
     int ngroup = 0;      // row groups
     int rows_max = 0;    // most rows in one group
@@ -252,13 +253,14 @@ struct PanelPart {
     const PanelStage *stage = nullptr;
     const u32 *ent = nullptr;
     const void *val = nullptr;
-    void *xh = nullptr;  // contiguous u16 / u32 copy of one x column, zero padded
+    void *xh = nullptr;  // u16 / u32 copy of nv x columns, interleaved by vector, zero padded
     u32 *gbar = nullptr; // grid barrier: arrivals, generation
 };
 
-// Most clusters of q CTAs of the panel kernel resident at once with `smem`
-// bytes of dynamic shared memory each (0 when the launch cannot fit).
-int panel_max_clusters(bool small, int q, size_t smem);
+// Most clusters of q CTAs of the panel kernel for nv vectors per pass
+// resident at once with `smem` bytes of dynamic shared memory each (0 when
+// the launch cannot fit).
+int panel_max_clusters(bool small, int nv, int q, size_t smem);
 
 // One matrix plan (A or A^T).
 struct Plan {
@@ -306,6 +308,9 @@ struct ffspmv_handle {
     int *d_status = nullptr;   // device status word (timeouts)
     // patterns of the odd entries of A and A^T for the GF(2) products
     ff::Gf2Pattern *gf2[2] = {nullptr, nullptr};
+    // x-panel plans of A and A^T for 2 and 4 vectors per pass, built on the
+    // first block that uses them when the plan is the x-panel layout
+    ff::Plan *multi[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };
 
 namespace ff {

@@ -23,9 +23,11 @@ int bin_of_length(long long L);
 long long bin_upper(int b);
 BinChoice heuristic_bin_choice(int b, double pm_fraction, int use_pm1);
 
+// panel_nv: vectors per pass of an x-panel plan (1, 2, or 4 when m <= 2^16)
 ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                             const long long *ptr, const int *col, const u32 *val,
-                            u32 m, const ffspmv_options &opt, const BinChoice *bins);
+                            u32 m, const ffspmv_options &opt, const BinChoice *bins,
+                            int panel_nv = 1);
 
 // Sub-plans over a subset of rows (the exhaustive search).
 struct PlanSource;
@@ -44,6 +46,7 @@ bool format_valid(int f, int bin, long long maxlen);
 // entry words and values (u32 here; stored as u16 when m <= 2^16).
 struct PanelHost {
     bool small = true;
+    int nv = 1;
     int q = 1, ngroup = 0, rows_max = 0, resident = 0, px = 0, pe = 0, eb = 0;
     size_t smem = 0;
     long long pcols = 0, nstage = 0, npm = 0, npad = 0;
@@ -55,11 +58,12 @@ struct PanelHost {
 // Rows longer than kPanelLong are left out (the caller adds split CSR
 // segments for them).  pm_on: +-1 entries (cls != 0) go to value-free
 // sections.  force_q: 1, 2 or 4 forces the cluster size, else the builder
-// picks it; max_clusters(q, small) gives the clusters of q CTAs resident at
-// once.  False when the matrix has nothing to stage or exceeds the layout's
+// picks it; nv: vectors per pass (1, 2, or 4 when m <= 2^16), x and the row
+// sums interleaved by vector; max_clusters(q, small) gives the clusters of q
+// CTAs resident at once.  False when the matrix has nothing to stage or exceeds the layout's
 // limits.
 bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *col, const u32 *val,
-                  const unsigned char *cls, u32 m, bool pm_on, int force_q,
+                  const unsigned char *cls, u32 m, bool pm_on, int force_q, int nv,
                   const std::function<int(int, bool)> &max_clusters, PanelHost &H);
 
 void transpose_csr(long long nrows, long long ncols, const long long *ptr,

@@ -514,15 +514,22 @@ static PlanParams params_of(const Phase &ph, int acc_wide)
 
 // ---------------------------------------------------------------------------
 // x-panel layout (PanelPart, ff_internal.cuh; the host half is panel.cu).
-// Contiguous u16 / u32 copy of one x column, for plans whose CTAs are not all
-// resident at once (their panel kernel cannot stage x itself).
-template <typename XT>
+// u16 / u32 copy of NV x columns, interleaved by vector (xs[i NV + k] =
+// x[i ldx + k]), for plans whose CTAs are not all resident at once (their
+// panel kernel cannot stage x itself).
+template <typename XT, int NV>
 __global__ void __launch_bounds__(256) k_x_stage(const u32 *__restrict__ x, long long ldx, long long n,
                                                  XT *__restrict__ xs)
 {
     const long long nth = (long long)gridDim.x * blockDim.x;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long done = 0;
+    if constexpr (NV > 1) {
+        for (long long i = t; i < n; i += nth)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) xs[i * NV + k] = (XT)__ldg(x + i * ldx + k);
+        return;
+    }
     if (ldx == 1 && ((uintptr_t)x & 15u) == 0) {
         // contiguous x: 16-byte loads, four elements each
         const long long n4 = n / 4;
@@ -637,13 +644,44 @@ __device__ __forceinline__ void st_release_gpu(u32 *p, u32 v)
 // async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-template <bool SMALL>
+// The x words of one column: NV interleaved elements of type XT.
+template <bool SMALL, int NV>
+struct PanelX {
+    typedef typename std::conditional<
+        (SMALL ? 2 : 4) * NV == 2, unsigned short,
+        typename std::conditional<(SMALL ? 2 : 4) * NV == 4, u32,
+                                  typename std::conditional<(SMALL ? 2 : 4) * NV == 8, uint2, uint4>::type>::type>::type W;
+    // element k of the column
+    static __device__ __forceinline__ u32 get(const W &w, int k)
+    {
+        if constexpr (SMALL) {
+            if constexpr (NV == 1) return (u32)w;
+            else if constexpr (NV == 2) return k ? w >> 16 : w & 0xffffu;
+            else return k == 0 ? w.x & 0xffffu : k == 1 ? w.x >> 16 : k == 2 ? w.y & 0xffffu : w.y >> 16;
+        } else {
+            if constexpr (NV == 1) return w;
+            else return k ? w.y : w.x;
+        }
+    }
+};
+
+// y = alpha A x + beta y for NV vectors at once (x: columns vcol..vcol+NV-1
+// of the block, interleaved in the staged copy; row sums [row][NV]).
+template <bool SMALL, int NV>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__restrict__ y, long long ldy,
         const Mod M, int *status, int skip_stage, int fused)
 {
     typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
+    // a lane's term: one row sum's (AT), or, for 16-bit residues and NV > 1,
+    // two vectors' u32 sums side by side in a u64 (each half stays below
+    // 2^32, the bound of a single row sum, so no carry crosses between them)
+    typedef typename std::conditional<SMALL && NV == 1, u32, u64>::type LT;
+    constexpr int VG = SMALL && NV > 1 ? 2 : 1;  // vectors per term
+    typedef PanelX<SMALL, NV> XC;
+    typedef typename XC::W XW;
+    static_assert(sizeof(XW) == sizeof(XT) * NV, "x word of a column");
     constexpr int VB = SMALL ? 2 : 4;
     constexpr int kWarps = kPanelConsumers / 32;
     extern __shared__ __align__(128) unsigned char panel_smem[];
@@ -671,11 +709,12 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         // CTA's bulk copies read
         const long long G = gridDim.x;
         const long long share = ((P.ncols + G - 1) / G + 7) / 8 * 8;
-        const long long lo = min(P.ncols, (long long)cta * share), hi = min(P.ncols, lo + share);
+        const long long lo = min(P.ncols, (long long)cta * share) * NV, hi = min(P.ncols, lo / NV + share) * NV;
         XT *xh = reinterpret_cast<XT *>(P.xh);
-        long long done = lo;
-        if (ldx == 1 && ((uintptr_t)x & 15u) == 0) {
-            // four 16-byte loads in flight per thread before their stores
+        long long done = lo;  // lo, hi: elements of the interleaved copy
+        if (ldx == NV && ((uintptr_t)x & 15u) == 0) {
+            // the NV columns are contiguous: four 16-byte loads in flight per
+            // thread before their stores
             const long long i1 = hi / 4;
             for (long long i0 = lo / 4 + t; i0 < i1; i0 += 4 * kPanelThreads) {
                 uint4 v[4];
@@ -697,11 +736,24 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 }
             }
             done = max(lo, hi / 4 * 4);
+            for (long long i = done + t; i < hi; i += kPanelThreads) xh[i] = (XT)__ldg(x + i);
+        } else if (NV > 1 && ldx % NV == 0 && ((uintptr_t)x & (4u * NV - 1u)) == 0) {
+            // one 4*NV-byte load per column
+            typedef typename std::conditional<NV == 4, uint4, uint2>::type VW;
+            for (long long i = lo / NV + t; i < hi / NV; i += kPanelThreads) {
+                const VW w = __ldg(reinterpret_cast<const VW *>(x + i * ldx));
+                const u32 *c = reinterpret_cast<const u32 *>(&w);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) xh[i * NV + k] = (XT)c[k];
+            }
+        } else {
+            for (long long i = lo / NV + t; i < hi / NV; i += kPanelThreads)
+#pragma unroll
+                for (int k = 0; k < NV; ++k) xh[i * NV + k] = (XT)__ldg(x + i * ldx + k);
         }
-        for (long long i = done + t; i < hi; i += kPanelThreads) xh[i] = (XT)__ldg(x + i * ldx);
         fence_proxy_async_global();
     }
-    for (u32 r = t; r < nr; r += kPanelThreads) acc[r] = 0;
+    for (u32 r = t; r < nr * NV; r += kPanelThreads) acc[r] = 0;
     __syncthreads();
     if (t == 0) {
         for (int b = 0; b < kPanelStages; ++b) {
@@ -772,7 +824,7 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 const bool newx = (a.xs & kPanelNewX) != 0;
                 desc[b] = make_uint4(a.nent, a.ngen, a.npg | (a.npp << 16), a.xs & kPanelSlotMask);  // published by the arrive
                 mbar_expect_tx(bar, newx ? (u32)PX : 0u);
-                if (newx) bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX, xh + (size_t)a.xoff * sizeof(XT), (u32)PX, bar);
+                if (newx) bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX, xh + (size_t)a.xoff * sizeof(XW), (u32)PX, bar);
             }
             __syncwarp();
         }
@@ -799,12 +851,13 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 for (u32 lb = w0 * 32u; lb < nl; lb += 32u * kWarps) {
                     const u32 tl = lb + lane, c = min(32u, nl - lb);
                     const bool valid = tl < nl, general = tl < nlg;
-                    u32 e[8];
-                    AT tm[8];
+                    u32 e[8], v[8];
+                    XW xw[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         e[u] = 0;
-                        tm[u] = 0;
+                        v[u] = 0;
+                        xw[u] = XW{};
                     }
                     if (valid) {
                         // entries of lane j of this 32-lane block: 4j..4j+3 and 4c+4j..4c+4j+3
@@ -813,7 +866,6 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                         e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
                         e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
                         if (general) {
-                            u32 v[8];
                             if (SMALL) {
                                 const uint4 w = *reinterpret_cast<const uint4 *>(vb + 2 * 8 * tl);
                                 v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
@@ -825,50 +877,74 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                                 v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
                                 v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
                             }
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
-                                tm[u] = SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
-                            }
-                        } else {
-                            // +-1 sections (Sec. 2.4.2): x or m - x, no value
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
-                                tm[u] = (AT)((e[u] & kPanelNeg) ? M.m - xv : xv);
-                            }
                         }
-                    }
-                    // the warp's last lanes of this stage are in registers (the terms
-                    // above read every loaded word): the buffer can be refilled
-                    // while the sums go on
-                    if (lb + 32u * kWarps >= nl) {
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(empty0 + 8u * b);
-                        released = true;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            xw[u] = *reinterpret_cast<const XW *>(xs + (e[u] & kPanelIdxMask) * sizeof(XW));
                     }
                     const bool pack = valid && (general ? tl < lpg : tl - nlg < lpp);
                     // packs sit in lanes [0, lpg) and [nlg, nlg + lpp): a warp-uniform test
-                    if (lb < lpg || (lb + 32u > nlg && lb < nlg + lpp)) {
-                        // segmented warp sum over the lanes of one row, then one atomic.
-                        // Packs of one row are adjacent within each section; a row
-                        // can have packs in both sections, so the +-1 packs get keys
-                        // of their own (the runs the sum joins must be contiguous)
-                        AT sum = 0;
-                        if (pack) sum = ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7]));
+                    const bool packwarp = lb < lpg || (lb + 32u > nlg && lb < nlg + lpp);
+                    // segmented warp sum over the lanes of one row, then one atomic.
+                    // Packs of one row are adjacent within each section; a row
+                    // can have packs in both sections, so the +-1 packs get keys
+                    // of their own (the runs the sum joins must be contiguous).
+                    // Bit i of seg: the lane 2^i further on is in the same run
+                    u32 seg = 0;
+                    bool head = false;
+                    if (packwarp) {
                         const u32 key = pack ? ((e[0] >> 16) | (general ? 0u : 0x20000u)) : (0x10000u + (u32)lane);
 #pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const AT o = __shfl_down_sync(0xffffffffu, sum, d);
-                            const u32 k2 = __shfl_down_sync(0xffffffffu, key, d);
-                            if (lane + d < 32 && k2 == key) sum += o;
+                        for (int i = 0; i < 5; ++i) {
+                            const u32 k2 = __shfl_down_sync(0xffffffffu, key, 1 << i);
+                            if (lane + (1 << i) < 32 && k2 == key) seg |= 1u << i;
                         }
                         const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
-                        if (pack && (lane == 0 || kp != key)) atomicAdd(acc + (key & 0xffffu), sum);
+                        head = pack && (lane == 0 || kp != key);
                     }
-                    if (valid && !pack) {
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> 16), tm[u]);
+                    for (int k = 0; k < NV; k += VG) {
+                        LT tm[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) tm[u] = 0;
+                        if (valid) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                LT tv = 0;
+#pragma unroll
+                                for (int h = 0; h < VG; ++h) {
+                                    const u32 xv = XC::get(xw[u], k + h);
+                                    // +-1 sections (Sec. 2.4.2): x or m - x, no value
+                                    const LT t1 = general ? (SMALL ? (LT)red32_lazy(v[u] * xv, M.m, mu32)
+                                                                   : (LT)red64((u64)v[u] * xv, M))
+                                                          : (LT)((e[u] & kPanelNeg) ? M.m - xv : xv);
+                                    tv |= t1 << (32 * h);
+                                }
+                                tm[u] = tv;
+                            }
+                        }
+                        if (k == 0 && lb + 32u * kWarps >= nl) {
+                            // the warp's last lanes of this stage are in registers (the
+                            // terms above read every loaded word): the buffer can be
+                            // refilled while the sums go on
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(empty0 + 8u * b);
+                            released = true;
+                        }
+                        if (packwarp) {
+                            LT sum = 0;
+                            if (pack) sum = ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7]));
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) {
+                                const LT o = __shfl_down_sync(0xffffffffu, sum, 1 << i);
+                                if (seg & (1u << i)) sum += o;
+                            }
+                            if (head) atomicAdd(reinterpret_cast<LT *>(acc + (e[0] >> 16) * NV + k), sum);
+                        }
+                        if (valid && !pack) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) atomicAdd(reinterpret_cast<LT *>(acc + (e[u] >> 16) * NV + k), tm[u]);
+                        }
                     }
                 }
             } else {
@@ -895,9 +971,11 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     // rows at a time: one 16-byte load of their partial sums from each CTA of
     // the cluster, for three groups of rows, all issued before any is used
     // (distributed shared memory answers slowly; loads in flight overlap).
+    // (row sums are taken flat: element f is row f / NV, vector f % NV)
     constexpr u32 G = 16 / sizeof(AT);
-    const u32 share = ((nr + q - 1) / q + G - 1) / G * G;
-    const u32 rb = min(nr, rank * share), re = min(nr, rb + share);
+    const u32 nf = nr * NV;
+    const u32 share = ((nf + q - 1) / q + G - 1) / G * G;
+    const u32 rb = min(nf, rank * share), re = min(nf, rb + share);
     for (u32 rg = rb + G * t; rg < re; rg += 3 * G * kPanelThreads) {
         uint4 part[3][4];
 #pragma unroll
@@ -926,7 +1004,8 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                     const u32 c[4] = {w.x, w.y, w.z, w.w};
                     sum += SMALL ? (u64)c[i] : ((u64)c[2 * i + 1] << 32 | c[2 * i]);
                 }
-                u32 *yp = y + (long long)(r0 + r + i) * ldy;
+                const u32 f = r + i;
+                u32 *yp = y + (long long)(r0 + f / NV) * ldy + f % NV;
                 *yp = combine(red64(sum, M), yp, false, M);
             }
         }
@@ -934,16 +1013,19 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     if (q > 1) cluster_sync_all();  // no CTA leaves while its sums are being read
 }
 
-template <bool SMALL>
-static void panel_set_smem(size_t smem)
+// The panel kernel instance for (16-bit residues, vectors per pass).
+typedef void (*PanelKernel)(const PanelPart, const u32 *, long long, u32 *, long long, const Mod, int *, int, int);
+static PanelKernel panel_kernel(bool small, int nv)
 {
-    cudaFuncSetAttribute(k_panel<SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (small) return nv == 4 ? k_panel<true, 4> : nv == 2 ? k_panel<true, 2> : k_panel<true, 1>;
+    return nv == 2 ? k_panel<false, 2> : k_panel<false, 1>;
 }
 
-int panel_max_clusters(bool small, int q, size_t smem)
+int panel_max_clusters(bool small, int nv, int q, size_t smem)
 {
-    if (small) panel_set_smem<true>(smem);
-    else panel_set_smem<false>(smem);
+    if (!(nv == 1 || nv == 2 || (nv == 4 && small))) return 0;
+    const PanelKernel kf = panel_kernel(small, nv);
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)q, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
@@ -956,9 +1038,7 @@ int panel_max_clusters(bool small, int q, size_t smem)
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    cudaError_t e = small ? cudaOccupancyMaxActiveClusters(&n, k_panel<true>, &cfg)
-                          : cudaOccupancyMaxActiveClusters(&n, k_panel<false>, &cfg);
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, kf, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -980,14 +1060,17 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const unsigned sb =
             (unsigned)std::max<long long>(1, std::min<long long>((P.ncols / 4 + 255) / 256, 8LL * std::max(nsm, 1)));
-        if (pp.small)
-            k_x_stage<unsigned short><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned short *)pp.xh);
-        else
-            k_x_stage<u32><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (u32 *)pp.xh);
+        unsigned short *xs16 = (unsigned short *)pp.xh;
+        u32 *xs32 = (u32 *)pp.xh;
+        if (pp.small && pp.nv == 4) k_x_stage<unsigned short, 4><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
+        else if (pp.small && pp.nv == 2) k_x_stage<unsigned short, 2><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
+        else if (pp.small) k_x_stage<unsigned short, 1><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
+        else if (pp.nv == 2) k_x_stage<u32, 2><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs32);
+        else k_x_stage<u32, 1><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs32);
         FF_CUDA(cudaGetLastError());
     }
-    if (pp.small) panel_set_smem<true>(pp.smem);
-    else panel_set_smem<false>(pp.smem);
+    const PanelKernel kf = panel_kernel(pp.small, pp.nv);
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(pp.ngroup * pp.q), 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
@@ -1004,8 +1087,7 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
     const u32 *xv = x + vcol;
     int *status = ctl ? ctl->status : nullptr;
     const int skip = ctl ? ctl->skip_stage : -1;
-    if (pp.small) FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<true>, pp, xv, ldx, yv, ldy, M, status, skip, fused));
-    else FF_CUDA(cudaLaunchKernelEx(&cfg, k_panel<false>, pp, xv, ldx, yv, ldy, M, status, skip, fused));
+    FF_CUDA(cudaLaunchKernelEx(&cfg, kf, pp, xv, ldx, yv, ldy, M, status, skip, fused));
     return FFSPMV_OK;
 }
 
@@ -1018,7 +1100,7 @@ static int next_chunk(int left, bool has_atomic)
 long long count_plan_launches(const Plan &P, int nvec)
 {
     if (P.nrows == 0) return 0;
-    long long n = P.panel.on ? (P.panel.ngroup <= P.panel.resident ? 1LL : 2LL) * nvec : 0;
+    long long n = P.panel.on ? (P.panel.ngroup <= P.panel.resident ? 1LL : 2LL) * (nvec / P.panel.nv) : 0;
     for (const Phase &ph : P.phases) {
         if (ph.segs.empty()) continue;
         for (int c0 = 0; c0 < nvec; c0 += next_chunk(nvec - c0, ph.has_atomic))
@@ -1033,8 +1115,10 @@ ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
 {
     const Mod M1 = make_mod(m, alpha, beta);
     if (P.panel.on) {
-        // panels first (every row written); the long rows' segments then add in
-        for (int v = 0; v < nvec; ++v) {
+        // panels first (every row written); the long rows' segments then add
+        // in.  A plan for NV vectors per pass takes blocks of a multiple of NV
+        if (nvec % P.panel.nv) return FFSPMV_ERR_ARG;
+        for (int v = 0; v < nvec; v += P.panel.nv) {
             ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st, ctl);
             if (r != FFSPMV_OK) return r;
         }

@@ -39,8 +39,11 @@ struct SEnt {
     u32 neg;  // +-1 sections: 1 for a -1 entry
 };
 
-inline int xbank_of(u32 idx, int xb) { return xb == 2 ? (int)((idx >> 1) & 31u) : (int)(idx & 31u); }
-inline int rbank_of(u32 row, int ab) { return ab == 4 ? (int)(row & 31u) : (int)(row & 15u); }
+// Bank of x element idx (xb bytes per column: 2, 4, 8 or 16) and of the row
+// sums of a row (ab bytes per row: 4 to 32); wider words are numbered by
+// their 4-byte bank group, so that distinct numbers mean distinct banks.
+inline int xbank_of(u32 idx, int xb) { return xb == 2 ? (int)((idx >> 1) & 31u) : (int)(idx % (128u / xb)); }
+inline int rbank_of(u32 row, int ab) { return (int)(row % (128u / ab)); }
 
 // Single entries keyed by (x bank, row-sum bank).
 struct Pool {
@@ -133,7 +136,7 @@ void split_packs(const std::vector<SEnt> &in, std::vector<std::vector<SEnt>> &pa
 // Lays out one stage: writes its entries (and the values of its general
 // lanes) and fills the counts of `st`.
 void lay_stage(const std::vector<SEnt> &ents, const std::vector<unsigned char> &is_pm, int xb, int ab,
-               std::vector<u32> &ent_out, std::vector<u32> &val_out, PanelStage &st, long long &npad,
+               bool small, std::vector<u32> &ent_out, std::vector<u32> &val_out, PanelStage &st, long long &npad,
                long long &npm)
 {
     std::vector<SEnt> gen, pm;
@@ -267,7 +270,7 @@ void lay_stage(const std::vector<SEnt> &ents, const std::vector<unsigned char> &
             const int pos = 8 * b0 + (u < 4 ? 4 * j + u : 4 * c + 4 * j + (u - 4));
             ent_out[st.k0 + pos] = (s.row << 16) | ((general ? 0u : s.neg) << 15) | s.idx;
             if (general) {
-                const int vpos = xb == 2 ? 8 * t + u : 8 * b0 + (u < 4 ? 4 * j + u : 4 * cg + 4 * j + (u - 4));
+                const int vpos = small ? 8 * t + u : 8 * b0 + (u < 4 ? 4 * j + u : 4 * cg + 4 * j + (u - 4));
                 val_out[st.v0 + vpos] = s.val;
             }
         }
@@ -295,7 +298,7 @@ std::vector<u32> row_groups(long long n, const std::function<long long(long long
 }  // namespace
 
 bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *col, const u32 *val,
-                  const unsigned char *cls, u32 m, bool pm_on, int force_q,
+                  const unsigned char *cls, u32 m, bool pm_on, int force_q, int nv,
                   const std::function<int(int, bool)> &max_clusters, PanelHost &H)
 {
     const std::function<long long(long long)> len = [&](long long i) {
@@ -306,7 +309,9 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     for (long long i = 0; i < n; ++i) nnz += len(i);
     if (n <= 0 || nc <= 0 || nnz == 0 || nnz >= (1LL << 31) || nc >= (1LL << 31) - 65536) return false;
     const bool small = m <= 65536u;
-    const int xb = small ? 2 : 4, vb = small ? 2 : 4, ab = small ? 4 : 8;
+    if (nv != 1 && nv != 2 && !(nv == 4 && small)) return false;
+    // bytes of x per column and of row sums per row: nv vectors interleaved
+    const int xb = (small ? 2 : 4) * nv, vb = small ? 2 : 4, ab = (small ? 4 : 8) * nv;
     const int ebytes = 4 + vb;
     const int min_sb = 8192 + 1024 * ebytes;
     const long long rcap = std::min<long long>(65536, (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
@@ -437,7 +442,7 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
                 // a new panel takes the slot of the panel kPanelStages back,
                 // whose stages all ended before the panels in between began
                 st.xs = (loaded % kPanelStages) | (k == b0 ? kPanelNewX : 0u);
-                lay_stage(chunk, chunk_pm, xb, ab, o.ent, o.val, st, o.npad, o.npm);
+                lay_stage(chunk, chunk_pm, xb, ab, small, o.ent, o.val, st, o.npad, o.npm);
                 o.st.push_back(st);
             }
             if (b1 > b0) ++loaded;
@@ -496,6 +501,7 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
         H.stage.push_back(st);
     }
     H.small = small;
+    H.nv = nv;
     H.q = q;
     H.ngroup = (int)ng;
     H.rows_max = (int)rows_max;
@@ -517,12 +523,12 @@ using namespace ff;
 // decoded back to (row, column, value) triples.  No device call is made.
 extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const int64_t *row_ptr,
                                              const int32_t *col, const uint32_t *values, uint32_t m,
-                                             int32_t use_pm1, int32_t q, int32_t clusters, int64_t cap,
+                                             int32_t use_pm1, int32_t q, int32_t nv, int32_t clusters, int64_t cap,
                                              int64_t *out_row, int64_t *out_col, uint32_t *out_val,
                                              int64_t *out_n, double *stats)
 {
-    if (nrows < 0 || ncols < 0 || !row_ptr || m < 2 || (q != 1 && q != 2 && q != 4) || clusters < 1 ||
-        !out_n || cap < 0)
+    if (nrows < 0 || ncols < 0 || !row_ptr || m < 2 || (q != 1 && q != 2 && q != 4) ||
+        (nv != 1 && nv != 2 && nv != 4) || clusters < 1 || !out_n || cap < 0)
         return FFSPMV_ERR_ARG;
     const long long nnz = row_ptr[nrows];
     std::vector<u32> v((size_t)nnz), c((size_t)nnz);
@@ -535,9 +541,9 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
     }
     PanelHost H;
     const bool ok = panel_layout(nrows, ncols, (const long long *)row_ptr, c.data(), v.data(), cls.data(), m,
-                                 use_pm1 == 1, q, [&](int cq, bool) { return cq == q ? clusters : 0; }, H);
+                                 use_pm1 == 1, q, nv, [&](int cq, bool) { return cq == q ? clusters : 0; }, H);
     if (!ok) return FFSPMV_ERR_UNSUPPORTED;
-    const int xb = H.small ? 2 : 4, ab = H.small ? 4 : 8;
+    const int xb = (H.small ? 2 : 4) * nv, ab = (H.small ? 4 : 8) * nv;  // bytes per column / per row
     long long n = 0, lanes = 0, packs = 0, bad_packs = 0;
     double gwf = 0, awf = 0, slots = 0, aslots = 0;
     for (long long cta = 0; cta < (long long)H.ngroup * H.q; ++cta) {
@@ -560,13 +566,13 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
                         w[u] = H.ent[st.k0 + pos];
                         u32 value;
                         if (general) {
-                            const int vpos = xb == 2 ? 8 * t + u : 8 * b0 + (u < 4 ? 4 * j + u : 4 * cg + 4 * j + (u - 4));
+                            const int vpos = H.small ? 8 * t + u : 8 * b0 + (u < 4 ? 4 * j + u : 4 * cg + 4 * j + (u - 4));
                             value = H.val[st.v0 + vpos];
                         } else {
                             value = (w[u] & kPanelNeg) ? m - 1u : 1u;
                         }
                         const u32 idx = w[u] & kPanelIdxMask;
-                        xw[u][nxw[u]++] = (int)(xb == 2 ? idx >> 1 : idx);
+                        xw[u][nxw[u]++] = (int)(xb == 2 ? idx >> 1 : idx * (u32)(xb / 4));  // first 4-byte word
                         if (!pack) rw[u][nrw[u]++] = (int)(w[u] >> 16);
                         if (value == 0) continue;  // padding
                         if (n < cap) {
@@ -600,7 +606,7 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
                     slots += 1;
                     if (nrw[u]) {
                         int bankr[32] = {0};
-                        for (int k = 0; k < nrw[u]; ++k) bankr[ab == 4 ? (rw[u][k] & 31) : (rw[u][k] & 15)]++;
+                        for (int k = 0; k < nrw[u]; ++k) bankr[rbank_of((u32)rw[u][k], ab)]++;
                         awf += *std::max_element(bankr, bankr + 32);
                         aslots += 1;
                     }

@@ -637,7 +637,7 @@ BinChoice heuristic_bin_choice(int b, double pm_fraction, int use_pm1)
 
 // x-panel layout: the host half (geometry, stages, entry order) is
 // panel_layout (panel.cu); this puts it into the plan's arena.
-bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPart &pp, size_t &o_grp,
+bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, int nv, PanelPart &pp, size_t &o_grp,
                 size_t &o_sptr, size_t &o_stage, size_t &o_ent, size_t &o_val, size_t &o_xh, size_t &o_bar)
 {
     long long npm = 0;
@@ -648,7 +648,8 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPar
     const bool pm_on = use_pm1 == 1 || (use_pm1 < 0 && nnz > 0 && npm * 20 >= nnz);
     PanelHost H;
     if (!panel_layout(A.nrows, A.ncols, A.ptr.data(), A.col.data(), A.val.data(), A.cls.data(), m, pm_on,
-                      force_q, [](int q, bool small) { return panel_max_clusters(small, q, kPanelSmemMax); }, H))
+                      force_q, nv, [nv](int q, bool small) { return panel_max_clusters(small, nv, q, kPanelSmemMax); },
+                      H))
         return false;
     const int vb = H.small ? 2 : 4, xb = H.small ? 2 : 4;
     std::vector<unsigned char> vbytes(H.val.size() * vb + 64, 0);
@@ -659,6 +660,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPar
     H.ent.resize(H.ent.size() + 16, 0);
     pp.on = true;
     pp.small = H.small;
+    pp.nv = H.nv;
     pp.q = H.q;
     pp.ngroup = H.ngroup;
     pp.rows_max = H.rows_max;
@@ -676,7 +678,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPar
     o_stage = B.putv(H.stage);
     o_ent = B.putv(H.ent);
     o_val = B.putv(vbytes);
-    std::vector<unsigned char> z((size_t)(A.ncols + H.pcols + 64) * xb, 0);
+    std::vector<unsigned char> z((size_t)(A.ncols + H.pcols + 64) * xb * H.nv, 0);
     o_xh = B.putv(z);
     std::vector<u32> bar(2, 0);  // grid barrier: arrivals, generation
     o_bar = B.putv(bar);
@@ -685,7 +687,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, PanelPar
 
 ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                             const long long *ptr, const int *col, const u32 *val,
-                            u32 m, const ffspmv_options &opt, const BinChoice *bins)
+                            u32 m, const ffspmv_options &opt, const BinChoice *bins, int panel_nv)
 {
     const Mat A = load_matrix(nrows, ncols, ptr, col, val, m);
     P.nrows = nrows;
@@ -886,8 +888,8 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
     case FFSPMV_FMT_PANEL: {
         name = "PANEL";
         size_t o_grp, o_sptr, o_stage, o_ent, o_val, o_xh, o_bar;
-        if (make_panel(B, A, m, upm, opt.panel_cluster, P.panel, o_grp, o_sptr, o_stage, o_ent, o_val, o_xh,
-                       o_bar)) {
+        if (make_panel(B, A, m, upm, opt.panel_cluster, panel_nv, P.panel, o_grp, o_sptr, o_stage, o_ent, o_val,
+                       o_xh, o_bar)) {
             // rows beyond kPanelLong: split CSR segments adding into y after the panels
             Rows huge;
             for (long long i = 0; i < nrows; ++i)
@@ -920,9 +922,11 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
         char buf[400];
         snprintf(buf, sizeof buf,
                  "  panels: %d row groups x %d column groups (clusters of %d, %d resident), %lld stages of %d B x"
-                 " + %d entries, x staged as %s, %s row sums, %lld entries in +-1 sections, %lld padding\n",
+                 " + %d entries, x staged as %s, %s row sums, %d vector(s) per pass, %lld entries in +-1 sections,"
+                 " %lld padding\n",
                  P.panel.ngroup, P.panel.q, P.panel.q, P.panel.resident, P.panel.nstage, P.panel.px, P.panel.pe,
-                 P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64", P.panel.npm, P.panel.npad);
+                 P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64", P.panel.nv, P.panel.npm,
+                 P.panel.npad);
         P.summary += buf;
         return FFSPMV_OK;
     }

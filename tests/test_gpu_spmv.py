@@ -149,6 +149,34 @@ def test_panel_timeout_hook_sets_status_and_handle_survives(lib):
     check_apply(lib, N, A, seed=4)
 
 
+@pytest.mark.parametrize("m,pm", [(65521, 0.3), (3, 1.0), (2**31 - 1, 0.2)])
+def test_panel_multi_vector_passes(lib, m, pm):
+    """Blocks on an x-panel handle run in passes of 4 (m <= 2^16) or 2
+    vectors, each reading the matrix once on a layout built for its width.
+    Widths 2 to 16 cover contiguous blocks (ldx = pass width), strided ones
+    (vector loads and scalar loads of x), and remainders of 2 and 1."""
+    A = gen.powerlaw_matrix(seed=17, n=60_007, lmax=4000, m=m, pm_fraction=pm)
+    M = make(lib, A, "PANEL", use_pm1=1 if pm else 0)
+    for nvec in (2, 3, 4, 6, 7, 16):
+        check_apply(lib, M, A, nvec=nvec, alpha=5 % m, beta=(m - 2) % m, seed=nvec)
+        check_apply(lib, M, A, nvec=nvec, transpose=True, seed=nvec + 50)
+    width = 4 if m <= 65536 else 2
+    assert M.launches(False, 16) == 16 // width     # one launch per pass
+
+
+def test_panel_staging_launch_when_groups_exceed_resident(lib):
+    """Row groups beyond the resident clusters: x is staged by a launch of
+    its own before the panel kernel (two launches per pass), for one vector
+    (32-bit residues, clusters of 4) and for passes of 4 vectors (16-bit
+    residues, whose row sums take 4x the shared memory per row)."""
+    n = 1_200_000
+    for m, q, nvec in ((2**31 - 1, 4, 1), (65521, 2, 4)):
+        A = gen.uniform_matrix(9, n, 200_000, np.full(n, 3), m, pm_fraction=0.2)
+        M = make(lib, A, "PANEL", panel_cluster=q, transpose_mode=lib.TRANSPOSE.NONE)
+        assert M.launches(False, nvec) == 2, M.describe()
+        check_apply(lib, M, A, nvec=nvec, alpha=3, beta=7, seed=q)
+
+
 @pytest.mark.parametrize("use_pm1", [0, 1])
 def test_panel_longest_rows_worst_values(lib, use_pm1):
     # m <= 2^16: general terms are reduced only below 2m, and a -1 entry's
@@ -169,6 +197,13 @@ def test_panel_longest_rows_worst_values(lib, use_pm1):
     y = to_host(M.apply(to_dev(x)))
     assert list(y) == [int(L) * (m - 1) * xv % m for L in lengths]
     check_apply(lib, M, A, alpha=2, beta=3, seed=6)
+    # passes of 2 and 4 vectors keep two u32 sums side by side in a u64:
+    # the same limit, with no carry from one into the other
+    for nvec in (2, 4):
+        X = np.full((nc, nvec), xv, dtype=np.uint32)
+        Y = to_host(M.apply(to_dev(X)))
+        assert all(list(Y[:, k]) == [int(L) * (m - 1) * xv % m for L in lengths] for k in range(nvec))
+        check_apply(lib, M, A, nvec=nvec, alpha=2, beta=3, seed=7)
 
 
 def test_rectangular_and_empty_rows(lib):

@@ -13,7 +13,7 @@ import gen
 from helpers import with_modulus
 
 
-def decode(A, m, use_pm1, q, clusters):
+def decode(A, m, use_pm1, q, clusters, nv=1):
     import paper_1004_3719_gb300 as ff
     ff.build()
     L = ff.lib()
@@ -27,7 +27,7 @@ def decode(A, m, use_pm1, q, clusters):
     n = ctypes.c_int64()
     st = (ctypes.c_double * 10)()
     rc = L.ffspmv_panel_decode(A.nrows, A.ncols, rp.ctypes.data, col.ctypes.data, val.ctypes.data, m,
-                               use_pm1, q, clusters, cap, r.ctypes.data, c.ctypes.data, v.ctypes.data,
+                               use_pm1, q, nv, clusters, cap, r.ctypes.data, c.ctypes.data, v.ctypes.data,
                                ctypes.byref(n), st)
     assert rc == 0
     return r[:n.value], c[:n.value], v[:n.value], list(st)
@@ -59,6 +59,38 @@ def test_layout_decodes_to_the_matrix(m, use_pm1, q):
         assert st[4] > 0                                # +-1 sections in use
     if m == 3 and use_pm1:
         assert st[4] >= 0.99 * A.nnz                    # all +-1 (up to the odd few per stage)
+
+
+@pytest.mark.parametrize("m,use_pm1,q,nv", [(65521, 1, 2, 2), (3, 1, 1, 4), (65521, 0, 4, 4),
+                                            (2**31 - 1, 1, 2, 2)])
+def test_multi_vector_layout_decodes_to_the_matrix(m, use_pm1, q, nv):
+    """The layouts of 2- and 4-vector passes (x and row sums interleaved by
+    vector, so smaller panels and row groups) hold the same entries, with
+    panel bytes a multiple of the interleaved column width."""
+    A = with_modulus(gen.powerlaw_matrix(seed=43, n=50_000, lmax=5000), m, pm_fraction=0.3, seed=5)
+    r, c, v, st = decode(A, m, use_pm1, q, 12, nv=nv)
+    assert st[8] == 0
+    assert same_triples((r, c, v), expected(A, m))
+    xb = (2 if m <= 65536 else 4) * nv
+    assert st[6] % 128 == 0 and st[6] % xb == 0
+    _, _, _, st1 = decode(A, m, use_pm1, q, 12, nv=1)
+    assert st[6] / xb <= st1[6] / (xb // nv)            # no more columns per panel than one vector's
+
+
+def test_multi_vector_layout_limits():
+    """Four vectors per pass only with 16-bit residues; nv outside 1, 2, 4 is
+    an argument error."""
+    import paper_1004_3719_gb300 as ff
+    A = with_modulus(gen.powerlaw_matrix(seed=44, n=5_000, lmax=500), 2**31 - 1, seed=1)
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(A.col, dtype=np.int32)
+    val = np.ascontiguousarray(A.val, dtype=np.uint32)
+    n = ctypes.c_int64()
+    L = ff.lib()
+    for nv, want in ((4, 5), (3, 1), (0, 1)):
+        rc = L.ffspmv_panel_decode(A.nrows, A.ncols, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                   2**31 - 1, 0, 1, nv, 8, 0, None, None, None, ctypes.byref(n), None)
+        assert rc == want, (nv, rc)
 
 
 def test_layout_with_duplicates_zeros_and_long_rows():
