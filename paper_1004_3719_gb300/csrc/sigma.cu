@@ -5,19 +5,19 @@
 // evaluation / pointwise / interpolation scheme), and M-Basis, the iterative
 // algorithm Sec. 3.2.2 recommends at small orders, as one CTA per leaf.
 //
-// M-Basis leaf.  For an order-d problem (d <= 32) the CTA keeps in shared
-// memory the residual R = P F (coefficients k..d-1, m x n each) and the basis
-// P (coefficients 0..k, m x m).  At order k one warp eliminates the m x n
-// matrix R_k column by column (rows ordered by (delta_i, i), pivot = the
-// first non-pivot row nonzero in the column); the whole CTA then applies the
-// same row operations to every coefficient of R and P, one thread per
-// (coefficient, column) position and thread-local in it, and multiplies the
-// pivot rows by x.  The elimination is fraction free -- row r becomes
-// a r - b q with a the pivot's entry and b row r's entry -- so no inverse is
-// taken inside the loop; each row of P is then a known nonzero multiple c_r
-// of the row that the elimination with division gives, and one inversion per
-// row at the end of the leaf divides it out, which makes the result the same
-// as the plain algorithm's.
+// M-Basis leaf.  An order-d problem (d <= 32) runs on one cluster of CTAs
+// that keep, column by column, the residual R = P F (coefficients k..d-1,
+// m x n) and the basis P (coefficients 0..k, m x m) in shared memory.  At
+// order k one warp eliminates the m x n matrix R_k column by column (rows
+// ordered by (delta_i, i), pivot = the first non-pivot row nonzero in the
+// column), one lane per row; every CTA then applies the same row operations
+// to its coefficients of R and P, one warp per (coefficient, column)
+// position, and multiplies the pivot rows by x.  The elimination is fraction
+// free -- row r becomes a r - b q with a the pivot's entry and b row r's
+// entry -- so no inverse is taken inside the loop; each row of P is then a
+// known nonzero multiple c_r of the row that the elimination with division
+// gives, and one inversion per row at the end of the leaf divides it out,
+// which makes the result the same as the plain algorithm's.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -33,9 +33,12 @@ namespace {
 constexpr int kSbMaxM = 32;                 // rows of F and of P (the polynomial-matrix product's limit)
 constexpr int kSbMaxBase = 32;              // largest leaf order
 constexpr int kSbThreads = 512;
+constexpr int kSbWarps = kSbThreads / 32;
+constexpr int kSbCluster = 8;               // CTAs of one leaf (portable cluster size)
 constexpr size_t kSbSmemMax = 227 * 1024;
 constexpr size_t kSbAlign = 256;
 constexpr int kSbMaxShift = 1 << 24;
+constexpr int kSbRkLd = kSbMaxM + 1;        // row stride of the leader's copy of R_k (no bank conflicts)
 
 struct SbLeaf {
     const u32 *F;   // d x m x ldf, columns < n used
@@ -46,19 +49,32 @@ struct SbLeaf {
     Mod M;
 };
 
-// shared memory of one leaf: R (d x m x n), P ((d+1) x m x m), the column
-// operations (multiplier and addend pairs, kSbMaxM x kSbMaxM), pivots, degrees,
-// pivot flags and the inverse row scales
-// words before the op table: R and P, rounded up to an even count so that the
-// 8-byte pairs are aligned
-__host__ __device__ inline size_t sb_op_offset(int m, int n, long long d)
-{
-    return ((size_t)d * m * n + (size_t)(d + 1) * m * m + 1) & ~(size_t)1;
-}
+// The operations of one order, as every CTA of the leaf receives them:
+// (multiplier, addend) of row r at column j in op[j][r], the pivot row of
+// column j (-1: none) and the pivot flags of the rows.
+struct SbOps {
+    uint2 op[kSbMaxM][kSbMaxM];
+    int piv[kSbMaxM];
+    int isp[kSbMaxM];
+};
+
+// CTAs of a leaf: one per column of [R | P] at most
+__host__ __device__ inline int sb_cluster(int m, int n) { return n + m < kSbCluster ? n + m : kSbCluster; }
+
+// Shared memory of one CTA of a leaf: the operations (two copies, by order
+// parity), the leader's copy of R_k, the inverse row scales, then the CTA's
+// columns of [R | P] (column w belongs to CTA w mod C), each (d+1) x m words
+// coefficient-major: word (t m + r) of a column is row r of coefficient t.
+constexpr size_t kSbOpsBytes = sizeof(SbOps);
+constexpr size_t kSbRkOff = 2 * kSbOpsBytes;
+constexpr size_t kSbInvOff = kSbRkOff + (size_t)kSbMaxM * kSbRkLd * 4;
+constexpr size_t kSbColOff = kSbInvOff + kSbMaxM * 4;
+static_assert(kSbOpsBytes % 16 == 0 && kSbColOff % 16 == 0, "16-byte blocks");
 
 size_t sb_leaf_smem(int m, int n, long long d)
 {
-    return (sb_op_offset(m, n, d) + 2 * kSbMaxM * kSbMaxM + 4 * kSbMaxM) * 4;
+    const int C = sb_cluster(m, n), own = (n + m + C - 1) / C;
+    return kSbColOff + (size_t)own * (size_t)(d + 1) * m * 4;
 }
 
 __device__ u32 sb_pow(u32 a, u32 e, const Mod &M)
@@ -72,156 +88,206 @@ __device__ u32 sb_pow(u32 a, u32 e, const Mod &M)
     return r;
 }
 
+// The same shared-memory word in CTA `rank` of the cluster.
+__device__ __forceinline__ u32 sb_remote(const void *local, u32 rank)
+{
+    u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((u32)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void sb_st_remote(u32 addr, u32 v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void sb_st_remote_v4(u32 addr, uint4 v)
+{
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// Every thread of every CTA of the cluster: writes before it are seen after it.
+__device__ __forceinline__ void sb_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ u32 sb_cluster_rank()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ u32 sb_cluster_size()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// One M-Basis leaf on a cluster of C CTAs (C = min(8, n + m)).  Each CTA
+// keeps its columns of [R | P] in shared memory; per order k:
+//   1. the leader's warp 0 eliminates R_k (gathered in the leader), one lane
+//      per row, and sends the operations to every CTA;
+//   2. every CTA applies them to its positions, one warp per (coefficient,
+//      column) position and one lane per row (R: coefficients k..d-1, P:
+//      0..k);
+//   3. the pivot rows of each column move up one coefficient (times x), and
+//      the owners of R's columns send R_{k+1} to the leader.
+// Two cluster barriers per order order these steps.
 __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_constant__ SbLeaf a)
 {
-    extern __shared__ __align__(16) u32 sb_sm[];
+    extern __shared__ __align__(16) unsigned char sb_sm[];
     const int m = a.m, n = a.n, d = a.d;
     const u32 p = a.M.m;
-    u32 *R = sb_sm;                                   // R[t][i][j] at (t m + i) n + j
-    u32 *P = R + (size_t)d * m * n;                   // P[t][i][l] at (t m + i) m + l
-    uint2 *sop = reinterpret_cast<uint2 *>(sb_sm + sb_op_offset(m, n, d));  // (multiplier, addend) of row r at column j: sop[j][r]
-    int *spiv = (int *)(sop + kSbMaxM * kSbMaxM);     // pivot row of column j, -1 if none
-    int *sdelta = spiv + kSbMaxM;
-    int *sisp = sdelta + kSbMaxM;                     // row is a pivot at this order
-    u32 *sinv = (u32 *)(sisp + kSbMaxM);              // 1 / c_r
-    const int tid = threadIdx.x;
+    const u32 rank = sb_cluster_rank(), C = sb_cluster_size();
+    const int own = (n + m - (int)rank + (int)C - 1) / (int)C;  // columns rank, rank + C, ...
+    SbOps *ops = reinterpret_cast<SbOps *>(sb_sm);
+    u32 *Rk = reinterpret_cast<u32 *>(sb_sm + kSbRkOff);   // leader: R_k row r at r * kSbRkLd
+    u32 *sinv = reinterpret_cast<u32 *>(sb_sm + kSbInvOff);
+    u32 *col = reinterpret_cast<u32 *>(sb_sm + kSbColOff);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cst = (d + 1) * m;   // words per column
 
-    for (long long i = tid; i < (long long)d * m * n; i += blockDim.x) {
-        const long long t = i / ((long long)m * n);
-        const int r = (int)((i / n) % m), c = (int)(i % n);
-        R[i] = red64(a.F[((size_t)t * m + r) * a.ldf + c], a.M);
+    // column i of this CTA is column w = rank + i C of [R | P]: R's column w
+    // (the input, reduced) when w < n, else P's column w - n (the identity)
+    for (int i = 0; i < own; ++i) {
+        const int w = (int)rank + i * (int)C;
+        u32 *cb = col + (size_t)i * cst;
+        for (int e = tid; e < cst; e += kSbThreads) {
+            const int t = e / m, r = e % m;
+            u32 v;
+            if (w < n) v = t < d ? red64(a.F[((size_t)t * m + r) * a.ldf + w], a.M) : 0u;
+            else v = (t == 0 && r == w - n) ? 1u : 0u;
+            cb[e] = v;
+        }
     }
-    for (long long i = tid; i < (long long)(d + 1) * m * m; i += blockDim.x) P[i] = 0;
     __syncthreads();
-    if (tid < m) {
-        P[(size_t)tid * m + tid] = 1u;
-        sdelta[tid] = a.shift[tid];
+    sb_cluster_sync();   // every CTA of the leaf runs before any remote store
+    for (int i = warp; i < own; i += kSbWarps) {
+        const int w = (int)rank + i * (int)C;
+        if (w < n && lane < m) sb_st_remote(sb_remote(Rk + lane * kSbRkLd + w, 0), col[(size_t)i * cst + lane]);
     }
-    __syncthreads();
-
-    u32 cs = 1u;   // warp 0, lane r < m: c_r, the product of the multipliers applied to row r
+    // leader's warp 0, lane r < m: delta_r and c_r, the product of the
+    // multipliers applied to row r
+    int dl = lane < m ? a.shift[lane] : 0;
+    u32 cs = 1u;
     for (int k = 0; k < d; ++k) {
-        if (tid < 32) {
-            // lane c holds column c of R_k; every lane holds the order positions
-            // of all rows; rows are indexed by constants only (registers)
-            const int lane = tid;
-            const int dl = lane < m ? sdelta[lane] : INT_MAX;
-            int myrank = 0;   // position of row `lane` in the order by (delta, index)
+        SbOps &O = ops[k & 1];
+        sb_cluster_sync();   // R_k is complete in the leader
+        if (rank == 0 && warp == 0) {
+            // rows ordered by (delta_i, i); the pivot of column j is the first
+            // row in that order, not yet a pivot, nonzero in the column
+            const bool row = lane < m;
+            int myrank = 0;
 #pragma unroll
             for (int j = 0; j < kSbMaxM; ++j) {
                 const int dj = __shfl_sync(0xffffffffu, dl, j);
                 myrank += (j < m && (dj < dl || (dj == dl && j < lane))) ? 1 : 0;
             }
-            int rk[kSbMaxM];
-            u32 v[kSbMaxM];
-#pragma unroll
-            for (int r = 0; r < kSbMaxM; ++r) {
-                rk[r] = __shfl_sync(0xffffffffu, myrank, r);
-                v[r] = (r < m && lane < n) ? R[((size_t)k * m + r) * n + lane] : 0u;
-            }
-            u32 pivots = 0u;   // bit r: row r is a pivot at this order
+            u32 *Rrow = Rk + lane * kSbRkLd;
+            u32 piv = 0u;   // bit r: row r is a pivot at this order
             for (int j = 0; j < n; ++j) {
-                // lane j: the first row in the order, not yet a pivot, nonzero in column j
-                int best = 64, q = -1;
-#pragma unroll
-                for (int r = 0; r < kSbMaxM; ++r) {
-                    if (r < m && !((pivots >> r) & 1u) && v[r] != 0u && rk[r] < best) {
-                        best = rk[r];
-                        q = r;
+                const u32 x = row ? Rrow[j] : 0u;
+                const bool cand = row && !((piv >> lane) & 1u) && x != 0u;
+                const u32 key = cand ? (u32)myrank : 64u;
+                const u32 mn = __reduce_min_sync(0xffffffffu, key);
+                uint2 myop = make_uint2(1u, 0u);
+                if (mn == 64u) {   // column j is already zero in every non-pivot row
+                    if (lane == 0) O.piv[j] = -1;
+                } else {
+                    const int q = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
+                    const u32 av = __shfl_sync(0xffffffffu, x, q);
+                    if (cand && lane != q) {
+                        // row <- av row - x pivot row (fraction free)
+                        const u32 g = p - x;
+                        const u32 *Rq = Rk + q * kSbRkLd;
+                        for (int c = j + 1; c < n; ++c) Rrow[c] = red64((u64)av * Rrow[c] + (u64)g * Rq[c], a.M);
+                        Rrow[j] = 0u;
+                        myop = make_uint2(av, g);
+                        cs = red64((u64)cs * av, a.M);
                     }
+                    piv |= 1u << q;
+                    if (lane == 0) O.piv[j] = q;
                 }
-                q = __shfl_sync(0xffffffffu, q, j);
-                best = __shfl_sync(0xffffffffu, best, j);
-                if (q < 0) {   // column j is already zero in every non-pivot row
-                    if (lane == 0) spiv[j] = -1;
-                    continue;
-                }
-                u32 vq = 0u;   // this lane's entry of the pivot row
-#pragma unroll
-                for (int r = 0; r < kSbMaxM; ++r) vq = (r == q) ? v[r] : vq;
-                const u32 av = __shfl_sync(0xffffffffu, vq, j);
-                u32 gmine = 0u;   // the addend coefficient of row `lane`
-#pragma unroll
-                for (int r = 0; r < kSbMaxM; ++r) {
-                    const u32 br = __shfl_sync(0xffffffffu, v[r], j);
-                    const bool upd = r < m && !((pivots >> r) & 1u) && br != 0u && rk[r] > best;
-                    const u32 g = upd ? p - br : 0u;   // nonzero exactly when row r is updated
-                    if (upd && lane > j && lane < n) v[r] = red64((u64)av * v[r] + (u64)g * vq, a.M);
-                    gmine = (lane == r) ? g : gmine;
-                }
-                if (lane < m) {
-                    sop[j * kSbMaxM + lane] = make_uint2(gmine ? av : 1u, gmine);
-                    if (gmine) cs = red64((u64)cs * av, a.M);
-                }
-                pivots |= 1u << q;
-                if (lane == 0) spiv[j] = q;
+                if (row) O.op[j][lane] = myop;
+                __syncwarp();   // the rows written at this column, before the next one reads them
             }
-            if (lane < m) {
-                const int ip = (pivots >> lane) & 1u;
-                sisp[lane] = ip;
-                if (ip) sdelta[lane] = dl + 1;
+            if (row) {
+                const int ip = (int)((piv >> lane) & 1u);
+                O.isp[lane] = ip;
+                dl += ip;
+            }
+            __syncwarp();
+            // the operations to the other CTAs: rows j < n of op[][], then piv and isp
+            const uint4 *src = reinterpret_cast<const uint4 *>(&O);
+            const uint4 *tail = reinterpret_cast<const uint4 *>(O.piv);
+            const int nq = n * (int)(kSbMaxM * sizeof(uint2) / 16);
+            for (u32 rr = 1; rr < C; ++rr) {
+                for (int e = lane; e < nq; e += 32) sb_st_remote_v4(sb_remote(src + e, rr), src[e]);
+                if (lane < (int)(2 * kSbMaxM * sizeof(int) / 16)) sb_st_remote_v4(sb_remote(tail + lane, rr), tail[lane]);
             }
         }
-        __syncthreads();
-        // the column operations, in order, on R's coefficients k..d-1 and P's 0..k
-        const int nr = (d - k) * n, np = (k + 1) * m;
-        for (int pos = tid; pos < nr + np; pos += blockDim.x) {
-            u32 *base;
-            int stride;
-            if (pos < nr) {
-                base = R + ((size_t)(k + pos / n) * m) * n + (pos % n);
-                stride = n;
-            } else {
-                const int w = pos - nr;
-                base = P + ((size_t)(w / m) * m) * m + (w % m);
-                stride = m;
+        sb_cluster_sync();   // the operations of order k are in every CTA
+        // positions: R's coefficients k..d-1 and P's 0..k of this CTA's columns
+        for (int pos = warp;; pos += kSbWarps) {
+            int i = 0, t = pos, w = 0;
+            for (; i < own; ++i) {
+                w = (int)rank + i * (int)C;
+                const int cnt = w < n ? d - k : k + 1;
+                if (t < cnt) break;
+                t -= cnt;
             }
-            u32 v[kSbMaxM];
-#pragma unroll
-            for (int r = 0; r < kSbMaxM; ++r) v[r] = r < m ? base[r * stride] : 0u;
+            if (i == own) break;
+            u32 *cell = col + (size_t)i * cst + (size_t)(w < n ? k + t : t) * m;
+            u32 v = lane < m ? cell[lane] : 0u;
             for (int j = 0; j < n; ++j) {
-                const int q = spiv[j];
+                const int q = O.piv[j];
                 if (q < 0) continue;
-                u32 vq = 0u;
-#pragma unroll
-                for (int r = 0; r < kSbMaxM; ++r) vq = (r == q) ? v[r] : vq;
-#pragma unroll
-                for (int r = 0; r < kSbMaxM; ++r) {
-                    if (r < m) {
-                        const uint2 op = sop[j * kSbMaxM + r];
-                        if (op.y) v[r] = red64((u64)op.x * v[r] + (u64)op.y * vq, a.M);
-                    }
+                const u32 vq = __shfl_sync(0xffffffffu, v, q);
+                if (lane < m) {
+                    const uint2 op = O.op[j][lane];
+                    if (op.y) v = red64((u64)op.x * v + (u64)op.y * vq, a.M);
                 }
             }
-#pragma unroll
-            for (int r = 0; r < kSbMaxM; ++r)
-                if (r < m) base[r * stride] = v[r];
+            if (lane < m) cell[lane] = v;
         }
         __syncthreads();
         // pivot rows times x: R's coefficients k..d-1 and P's 0..k+1 move up by one
-        for (int w = tid; w < m * (n + m); w += blockDim.x) {
-            const int q = w / (n + m), c = w % (n + m);
-            if (!sisp[q]) continue;
-            if (c < n) {
-                for (int t = d - 1; t > k; --t)
-                    R[((size_t)t * m + q) * n + c] = R[((size_t)(t - 1) * m + q) * n + c];
-                R[((size_t)k * m + q) * n + c] = 0u;
-            } else {
-                const int l = c - n;
-                for (int t = k + 1; t > 0; --t)
-                    P[((size_t)t * m + q) * m + l] = P[((size_t)(t - 1) * m + q) * m + l];
-                P[(size_t)q * m + l] = 0u;
+        for (int i = warp; i < own; i += kSbWarps) {
+            const int w = (int)rank + i * (int)C;
+            u32 *cb = col + (size_t)i * cst;
+            if (lane < m && O.isp[lane]) {
+                if (w < n) {
+                    for (int t = d - 1; t > k; --t) cb[t * m + lane] = cb[(t - 1) * m + lane];
+                    cb[k * m + lane] = 0u;
+                } else {
+                    for (int t = k + 1; t > 0; --t) cb[t * m + lane] = cb[(t - 1) * m + lane];
+                    cb[lane] = 0u;
+                }
             }
+            if (w < n && k + 1 < d && lane < m)
+                sb_st_remote(sb_remote(Rk + lane * kSbRkLd + w, 0), cb[(k + 1) * m + lane]);
         }
-        __syncthreads();
     }
-    if (tid < m) sinv[tid] = sb_pow(cs, p - 2u, a.M);   // c_r != 0 in the field F_p
-    __syncthreads();
-    for (long long i = tid; i < (long long)(d + 1) * m * m; i += blockDim.x) {
-        const int r = (int)((i / m) % m);
-        a.P[i] = red64((u64)P[i] * sinv[r], a.M);
+    sb_cluster_sync();
+    if (rank == 0 && warp == 0 && lane < m) {
+        const u32 inv = sb_pow(cs, p - 2u, a.M);   // c_r != 0 in the field F_p
+        for (u32 rr = 0; rr < C; ++rr) sb_st_remote(sb_remote(sinv + lane, rr), inv);
+        a.delta[lane] = dl;
     }
-    if (tid < m) a.delta[tid] = sdelta[tid];
+    sb_cluster_sync();   // the scales are in every CTA; no remote access after this
+    for (int i = 0; i < own; ++i) {
+        const int w = (int)rank + i * (int)C;
+        if (w < n) continue;
+        const u32 *cb = col + (size_t)i * cst;
+        for (int e = tid; e < cst; e += kSbThreads) {
+            const int t = e / m, r = e % m;
+            a.P[((size_t)t * m + r) * m + (w - n)] = red64((u64)cb[e] * sinv[r], a.M);
+        }
+    }
 }
 
 // Fp[k][i][j] = F[k][i][j] mod p for j < n, 0 for n <= j < m (square for the products)
@@ -347,8 +413,20 @@ ffspmv_status sb_leaf(SbRun &R, const u32 *F, long long d, const int *shift, u32
     a.d = (int)d;
     a.ldf = R.m;
     a.M = R.M;
-    k_sb_mbasis<<<1, kSbThreads, sb_leaf_smem(R.m, R.n, d), R.st>>>(a);
-    FF_CUDA(cudaGetLastError());
+    const unsigned C = (unsigned)sb_cluster(R.m, R.n);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kSbThreads, 1, 1);
+    cfg.dynamicSmemBytes = sb_leaf_smem(R.m, R.n, d);
+    cfg.stream = R.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FF_CUDA(cudaLaunchKernelEx(&cfg, k_sb_mbasis, a));
     FF_CUDA(cudaMemcpyAsync(delta, R.d_delta, sizeof(int) * R.m, cudaMemcpyDeviceToHost, R.st));
     FF_CUDA(cudaStreamSynchronize(R.st));
     return FFSPMV_OK;

@@ -60,7 +60,8 @@ def test_host_side_argument_errors_without_gpu():
     assert L.polymat_mul(1, 4, 1, 1, None, None, None, None, 0, None) == 1  # p >= 2, pointers
     assert L.sigma_basis_workspace(33, 16, 10, 0, ctypes.byref(n)) == 1      # m <= 32
     assert L.sigma_basis_workspace(8, 9, 10, 0, ctypes.byref(n)) == 1        # n <= m
-    assert L.sigma_basis_workspace(32, 32, 10, 32, ctypes.byref(n)) == 5     # leaf over shared memory
+    assert L.sigma_basis_workspace(32, 32, 10, 33, ctypes.byref(n)) == 1     # leaf order <= 32
+    assert L.sigma_basis_workspace(32, 32, 10, 32, ctypes.byref(n)) == 0     # a cluster holds any order-32 leaf
     assert L.sigma_basis_workspace(32, 16, 30000, 0, ctypes.byref(n)) == 5   # products past 2^15 points
     assert L.sigma_basis_workspace(32, 16, 12502, 0, ctypes.byref(n)) == 0
     d = ctypes.c_int32(0)

@@ -38,7 +38,9 @@ def _gpu(lib, p, F, shift=None, base=0):
     (65521, 5, 3, 23, 3, [1, 0, 0, 2, 0], 1.0),       # odd m, n and leaf orders
     (65521, 32, 16, 20, 8, None, 1.0),                # the width of s = 16 block Wiedemann
     (65521, 32, 16, 32, 32, None, 1.0),               # one leaf of the largest order
-    (1000003, 32, 32, 18, 16, None, 1.0),             # square, the default leaf order for it
+    (1000003, 32, 32, 18, 16, None, 1.0),             # square
+    (1000003, 32, 32, 40, 32, None, 1.0),             # square, order-32 leaves over a cluster of 8 CTAs
+    (65521, 3, 1, 9, 0, [0, 4, 1], 1.0),              # four columns: a cluster of four CTAs
 ])
 def test_parity_with_oracle(lib, p, m, n, d, base, shift, density):
     rng = np.random.default_rng(d * 131 + m)
