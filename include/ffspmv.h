@@ -45,8 +45,8 @@ typedef enum {
 
 /* Storage formats (Sec. 2.1 and 2.4).  FFSPMV_FMT_AUTO, decided separately
  * for A and A^T, by opt.selector:
- *   HEURISTIC (and FIXED): the x-panel layout when m <= 2^16, nnz >= 2^21
- *     and nnz >= 3 * ncols, else the binned layout with the heuristic table;
+ *   HEURISTIC (and FIXED): the x-panel layout when nnz >= 2^21 and nnz >=
+ *     3 * ncols, else the binned layout with the heuristic table;
  *   LEARNED: the layout of least predicted whole-plan time among x-panel,
  *     binned with the network's per-bin table and binned with the heuristic
  *     table (the network's matrix-level outputs); without installed weights,

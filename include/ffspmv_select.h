@@ -115,14 +115,23 @@ ffspmv_status ffspmv_selector_load(const float *params, int64_t count);
  * FFSPMV_LAYOUT_BINNED (the binned layout with the heuristic table),
  * FFSPMV_LAYOUT_NETBINS (the binned layout with best[][]) or
  * FFSPMV_LAYOUT_PANEL_Q1/Q2/Q4 (the x-panel layout with clusters of 1, 2 or
- * 4 CTAs).  This is what FFSPMV_SEL_LEARNED builds under FFSPMV_FMT_AUTO. */
+ * 4 CTAs) or FFSPMV_LAYOUT_PANEL (x-panel, the builder's cluster size).  A
+ * cluster size is named only when its predicted time beats the other two by
+ * FFSPMV_SEL_Q_MARGIN (log ratio), and the network's own table only when it
+ * beats the best other layout by FFSPMV_SEL_NET_MARGIN: that output is
+ * learned from the exhaustive search's table, which the network's table
+ * only approaches.  This is what FFSPMV_SEL_LEARNED builds under
+ * FFSPMV_FMT_AUTO. */
 enum {
     FFSPMV_LAYOUT_BINNED = 0,
     FFSPMV_LAYOUT_NETBINS = 1,
     FFSPMV_LAYOUT_PANEL_Q1 = 2,
     FFSPMV_LAYOUT_PANEL_Q2 = 3,
-    FFSPMV_LAYOUT_PANEL_Q4 = 4
+    FFSPMV_LAYOUT_PANEL_Q4 = 4,
+    FFSPMV_LAYOUT_PANEL = 5
 };
+#define FFSPMV_SEL_Q_MARGIN 0.05f
+#define FFSPMV_SEL_NET_MARGIN 0.15f
 ffspmv_status ffspmv_selector_choose(int64_t nrows, int64_t ncols, int64_t nnz,
                                      const int64_t *row_ptr, const int32_t *col,
                                      const uint32_t *values, uint32_t modulus, int32_t *best,

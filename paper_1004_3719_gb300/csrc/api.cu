@@ -60,14 +60,17 @@ void destroy_handle(ffspmv_handle *h)
     delete h;
 }
 
-// FFSPMV_FMT_AUTO takes the x-panel layout where it beat the binned one on
-// every measured shape: residues below 2^16 (u16 x and values, u32 row sums),
-// at least 2^21 entries (enough to fill the stage pipelines of all SMs) and
-// at least 3 entries per column (each column of x streamed through shared
-// memory serves several entries).  Elsewhere AUTO is BINNED.
+// FFSPMV_FMT_AUTO (heuristic selector) takes the x-panel layout where it beat
+// the binned one on every measured shape: at least 2^21 entries (enough to
+// fill the stage pipelines of all SMs) and at least 3 entries per column
+// (each column of x streamed through shared memory serves several entries),
+// at any modulus (u64 row sums at m > 2^16: 93 vs 101 us on the 1M power-law
+// matrix, 106-158 vs 211-246 us on held-out 34M-entry matrices).  Elsewhere
+// AUTO is BINNED.
 bool panel_preferred(long long ncols, long long nnz, u32 m)
 {
-    return m <= 65536u && nnz >= (1LL << 21) && nnz >= 3 * ncols;
+    (void)m;
+    return nnz >= (1LL << 21) && nnz >= 3 * ncols;
 }
 
 // Mean milliseconds of one y = A x with plan P (x = 0, y scratch), after warm-up.
@@ -147,7 +150,8 @@ ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
         const bool panel = layout >= FFSPMV_LAYOUT_PANEL_Q1 || (layout < 0 && panel_preferred(ncols, ptr[nrows], m));
         if (panel && ptr[nrows] > 0) {
             o2.priority_format = FFSPMV_FMT_PANEL;
-            if (layout >= FFSPMV_LAYOUT_PANEL_Q1) o2.panel_cluster = 1 << (layout - FFSPMV_LAYOUT_PANEL_Q1);
+            if (layout >= FFSPMV_LAYOUT_PANEL_Q1 && layout <= FFSPMV_LAYOUT_PANEL_Q4)
+                o2.panel_cluster = 1 << (layout - FFSPMV_LAYOUT_PANEL_Q1);
             Plan Q;
             if (build_plan_ex(Q, nrows, ncols, ptr, col, val, m, o2, nullptr) == FFSPMV_OK && Q.panel.on) {
                 P = Q;

@@ -596,17 +596,20 @@ ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, c
     if (layout) {
         // least predicted whole-plan time, relative to the heuristic binned plan (0)
         const float *o = &hout[kBins * kOut];
+        int kq = 0;
+        for (int k = 1; k < 3; ++k)
+            if (o[FFSPMV_OUT_PANEL + k] < o[FFSPMV_OUT_PANEL + kq]) kq = k;
+        float second = 1e30f;
+        for (int k = 0; k < 3; ++k)
+            if (k != kq) second = fminf(second, o[FFSPMV_OUT_PANEL + k]);
+        const float tp = o[FFSPMV_OUT_PANEL + kq];
         *layout = FFSPMV_LAYOUT_BINNED;
         float bestv = 0.f;
-        if (o[FFSPMV_OUT_NETBINS] < bestv) {
-            bestv = o[FFSPMV_OUT_NETBINS];
-            *layout = FFSPMV_LAYOUT_NETBINS;
+        if (tp < bestv) {
+            bestv = tp;
+            *layout = second - tp > FFSPMV_SEL_Q_MARGIN ? FFSPMV_LAYOUT_PANEL_Q1 + kq : FFSPMV_LAYOUT_PANEL;
         }
-        for (int k = 0; k < 3; ++k)
-            if (o[FFSPMV_OUT_PANEL + k] < bestv) {
-                bestv = o[FFSPMV_OUT_PANEL + k];
-                *layout = FFSPMV_LAYOUT_PANEL_Q1 + k;
-            }
+        if (o[FFSPMV_OUT_NETBINS] < bestv - FFSPMV_SEL_NET_MARGIN) *layout = FFSPMV_LAYOUT_NETBINS;
     }
     return FFSPMV_OK;
 }

@@ -42,15 +42,16 @@ ROOT = os.path.dirname(HERE)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from paper_1004_3719_gb300._lib import (LAYOUT_BINNED, LAYOUT_NETBINS,  # noqa: E402
+from paper_1004_3719_gb300._lib import (LAYOUT_BINNED, LAYOUT_NETBINS, LAYOUT_PANEL,  # noqa: E402
                                        LAYOUT_PANEL_Q1, LAYOUT_PANEL_Q2, LAYOUT_PANEL_Q4,
                                        MATRIX_INPUT, MLP_OUT, NUM_BIN_FEATURES, NUM_BINS,
-                                       NUM_FORMATS, OUT_NETBINS, OUT_PANEL, OUT_PM)
+                                       NUM_FORMATS, OUT_NETBINS, OUT_PANEL, OUT_PM,
+                                       SEL_NET_MARGIN, SEL_Q_MARGIN)
 
 # whole-plan timing keys: binned with the heuristic table (H) and with the
 # exhaustive table (E), x-panel with clusters of 1, 2 and 4 CTAs (P1, P2, P4)
 LAYOUT_KEY = {LAYOUT_BINNED: "H", LAYOUT_NETBINS: "E", LAYOUT_PANEL_Q1: "P1",
-              LAYOUT_PANEL_Q2: "P2", LAYOUT_PANEL_Q4: "P4"}
+              LAYOUT_PANEL_Q2: "P2", LAYOUT_PANEL_Q4: "P4", LAYOUT_PANEL: "P"}
 
 
 def _make(args):
@@ -104,9 +105,9 @@ def matrix_sample(feat, plan_us):
 
 def panel_rule(A):
     """The layout FMT.AUTO takes under the heuristic selector (the rule of
-    panel_preferred in csrc/api.cu): x-panel when m <= 2^16, nnz >= 2^21 and
-    nnz >= 3 ncols."""
-    return A.modulus <= 65536 and A.nnz >= (1 << 21) and A.nnz >= 3 * A.ncols
+    panel_preferred in csrc/api.cu): x-panel when nnz >= 2^21 and nnz >=
+    3 ncols."""
+    return A.nnz >= (1 << 21) and A.nnz >= 3 * A.ncols
 
 
 def time_handle(ff, M, x, y, flush, reps=7):
@@ -344,7 +345,7 @@ def main():
                   for k in ("learned", "heuristic", "exhaustive")} if whole else {}
     layouts = {n: int(sum(1 for w in whole if w["layout"] == v))
                for n, v in (("binned", LAYOUT_BINNED), ("netbins", LAYOUT_NETBINS), ("panel_q1", LAYOUT_PANEL_Q1),
-                            ("panel_q2", LAYOUT_PANEL_Q2), ("panel_q4", LAYOUT_PANEL_Q4))}
+                            ("panel_q2", LAYOUT_PANEL_Q2), ("panel_q4", LAYOUT_PANEL_Q4), ("panel", LAYOUT_PANEL))}
     total_us = {k: float(sum(w[k + "_us"] for w in whole)) for k in ("learned", "heuristic")}
     e2e = end_to_end(ff, sel, test_recs[:args.e2e], args) if args.e2e > 0 else []
     result = dict(train_matrices=len(train_recs), test_matrices=len(test_recs),
@@ -374,13 +375,25 @@ def learned_choice(net, r):
             continue
         scores = np.where(valid, out[b, :NUM_FORMATS], np.inf)
         best[b] = [int(np.argmin(scores)), int(out[b, OUT_PM] < 0), 1]
+    return best, layout_rule(out[NUM_BINS])
+
+
+def layout_rule(o):
+    """The library's whole-plan rule on the matrix-level outputs o: the
+    least predicted time (the heuristic binned plan counting 0); a cluster
+    size only when it beats the other two by SEL_Q_MARGIN, else the
+    builder's; the network's own table only when it beats the best other
+    layout by SEL_NET_MARGIN."""
+    pq = [float(o[OUT_PANEL + i]) for i in range(3)]
+    kq = int(np.argmin(pq))
+    second = min(pq[i] for i in range(3) if i != kq)
     layout, v = LAYOUT_BINNED, 0.0
-    if out[NUM_BINS, OUT_NETBINS] < v:
-        layout, v = LAYOUT_NETBINS, out[NUM_BINS, OUT_NETBINS]
-    for i, lay in enumerate((LAYOUT_PANEL_Q1, LAYOUT_PANEL_Q2, LAYOUT_PANEL_Q4)):
-        if out[NUM_BINS, OUT_PANEL + i] < v:
-            layout, v = lay, out[NUM_BINS, OUT_PANEL + i]
-    return best, layout
+    if pq[kq] < v:
+        v = pq[kq]
+        layout = (LAYOUT_PANEL_Q1 + kq) if second - pq[kq] > SEL_Q_MARGIN else LAYOUT_PANEL
+    if float(o[OUT_NETBINS]) < v - SEL_NET_MARGIN:
+        layout = LAYOUT_NETBINS
+    return layout
 
 
 def end_to_end(ff, sel, recs, args):
