@@ -160,7 +160,7 @@ def traffic_record(kernel_key):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "plan.cu", "ff_internal.cuh"):
+    for f in ("kernels.cu", "plan.cu", "panel.cu", "ff_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1004_3719_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

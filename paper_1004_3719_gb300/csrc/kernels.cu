@@ -554,18 +554,23 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// 16 bytes at the same shared-memory offset in CTA `rank` of the cluster.
+// The shared::cluster address of `local` in CTA `rank` of the cluster.
 template <typename T>
-__device__ __forceinline__ uint4 ld_cluster_v4(const T *local, u32 rank)
+__device__ __forceinline__ u32 map_cluster(const T *local, u32 rank)
 {
-    u32 a = (u32)__cvta_generic_to_shared(local), r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    uint4 v;
-    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(r)
-                 : "memory");
-    return v;
+    u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((u32)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+
+// *addr += v in another CTA's shared memory (posted; ordered by the next cluster barrier).
+__device__ __forceinline__ void red_cluster_add(u32 addr, u32 v)
+{
+    asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_cluster_add(u32 addr, u64 v)
+{
+    asm volatile("red.shared::cluster.add.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
 }
 
 // A value in [0, 2m) congruent to t mod m, for t < 2^32 and mu = floor(2^32 / m):
@@ -977,51 +982,33 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         }
         __syncthreads();
     }
-    if (q > 1) cluster_sync_all();  // every partial sum of the cluster is final
-    // This CTA finishes a share of the rows.  A thread takes G consecutive
-    // rows at a time: one 16-byte load of their partial sums from each CTA of
-    // the cluster, for three groups of rows, all issued before any is used
-    // (distributed shared memory answers slowly; loads in flight overlap).
-    // (row sums are taken flat: element f is row f / NV, vector f % NV)
+    // Row sums are taken flat: element f is row f / NV, vector f % NV.  CTA j
+    // of the cluster finishes the elements [j share, (j + 1) share): every
+    // other CTA adds its partial sums of them into CTA j's with distributed
+    // shared-memory reductions, posted as soon as its own stages are done
+    // (while slower CTAs still sum), and one cluster barrier makes them
+    // final.  A partial sum and the total are both sums of a row's terms, so
+    // they stay below the same bound as a single CTA's row sum.
     constexpr u32 G = 16 / sizeof(AT);
     const u32 nf = nr * NV;
     const u32 share = ((nf + q - 1) / q + G - 1) / G * G;
-    const u32 rb = min(nf, rank * share), re = min(nf, rb + share);
-    for (u32 rg = rb + G * t; rg < re; rg += 3 * G * kPanelThreads) {
-        uint4 part[3][4];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const u32 r = rg + (u32)k * G * kPanelThreads;
-            if (r < re) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (j < q)
-                        part[k][j] = (q > 1 && j != rank) ? ld_cluster_v4(acc + r, (u32)j)
-                                                          : *reinterpret_cast<const uint4 *>(acc + r);
+    if (q > 1) {
+        for (int j = 0; j < q; ++j) {
+            if (j == rank) continue;
+            const u32 jb = min(nf, (u32)j * share), je = min(nf, jb + share);
+            const u32 base = map_cluster(acc, (u32)j);
+            for (u32 f = jb + t; f < je; f += kPanelThreads) {
+                const AT v = acc[f];
+                if (v) red_cluster_add(base + f * (u32)sizeof(AT), v);
             }
         }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const u32 r = rg + (u32)k * G * kPanelThreads;
-            if (r >= re) break;
-#pragma unroll
-            for (u32 i = 0; i < G; ++i) {
-                if (r + i >= re) break;
-                u64 sum = 0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (j >= q) break;
-                    const uint4 w = part[k][j];
-                    const u32 c[4] = {w.x, w.y, w.z, w.w};
-                    sum += SMALL ? (u64)c[i] : ((u64)c[2 * i + 1] << 32 | c[2 * i]);
-                }
-                const u32 f = r + i;
-                u32 *yp = y + (long long)(r0 + f / NV) * ldy + f % NV;
-                *yp = combine(red64(sum, M), yp, false, M);
-            }
-        }
+        cluster_sync_all();  // every partial sum of this CTA's share has arrived
     }
-    if (q > 1) cluster_sync_all();  // no CTA leaves while its sums are being read
+    const u32 rb = min(nf, rank * share), re = min(nf, rb + share);
+    for (u32 f = rb + t; f < re; f += kPanelThreads) {
+        u32 *yp = y + (long long)(r0 + f / NV) * ldy + f % NV;
+        *yp = combine(red64((u64)acc[f], M), yp, false, M);
+    }
 }
 
 // The panel kernel instance for (16-bit residues, vectors per pass).
