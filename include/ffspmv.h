@@ -97,7 +97,8 @@ typedef struct {
                                   bounded wait of every other CTA runs out (FFSPMV_ERR_TIMEOUT);
                                   bit 1 = the x-panel kernel never issues the copies of the second
                                   stage of each CTA, so the waits for it run out (the status word
-                                  read by spmv_check_status) */
+                                  read by spmv_check_status); bit 2 = x-panel blocks always take
+                                  the 2- and 4-vector passes, without the timing that decides it */
     int32_t panel_cluster;     /* x-panel layout: CTAs per cluster (column groups); 0 = chosen by
                                   the builder, 1, 2 or 4 to force one */
 } ffspmv_options;
@@ -131,8 +132,9 @@ ffspmv_status spmv_create_hybrid(ffspmv_t *out, int64_t nrows, int64_t ncols,
  * plan is the x-panel layout, a block runs in passes of 4 vectors (m <=
  * 2^16) or 2, then 1: each pass reads the matrix once for all its vectors
  * (Sec. 2.5.1) on an x-panel layout built for that width; the first block
- * that needs a width builds its layout (synchronous, host work plus one
- * allocation per handle, direction and width).  Calls on one handle must not
+ * that needs a width builds its layout and times one pass of it against the
+ * same vectors one at a time (synchronous, host work plus one allocation
+ * per handle, direction and width), and keeps it only if it is faster.  Calls on one handle must not
  * overlap on the GPU (the x-panel plans stage x in buffers of the handle).
  */
 ffspmv_status spmv_apply(ffspmv_t h, const uint32_t *d_x, int64_t ldx,

@@ -73,22 +73,22 @@ bool panel_preferred(long long ncols, long long nnz, u32 m)
     return nnz >= (1LL << 21) && nnz >= 3 * ncols;
 }
 
-// Mean milliseconds of one y = A x with plan P (x = 0, y scratch), after warm-up.
-float time_whole_plan(const Plan &P, u32 m)
+// Mean milliseconds of one Y = A X with plan P for nvec vectors (X = 0, Y
+// scratch), after warm-up.
+float time_whole_plan(const Plan &P, u32 m, int nvec = 1)
 {
     u32 *x = nullptr, *y = nullptr;
     float ms = -1.0f;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaMalloc(&x, (size_t)std::max<long long>(P.ncols, 1) * 4) == cudaSuccess &&
-        cudaMalloc(&y, (size_t)std::max<long long>(P.nrows, 1) * 4) == cudaSuccess &&
-        cudaMemset(x, 0, (size_t)std::max<long long>(P.ncols, 1) * 4) == cudaSuccess &&
+    const size_t xb = (size_t)std::max<long long>(P.ncols, 1) * 4 * nvec, yb = (size_t)std::max<long long>(P.nrows, 1) * 4 * nvec;
+    if (cudaMalloc(&x, xb) == cudaSuccess && cudaMalloc(&y, yb) == cudaSuccess && cudaMemset(x, 0, xb) == cudaSuccess &&
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
         const int reps = 5;
-        for (int w = 0; w < 2; ++w) run_plan(P, x, 1, y, 1, 1, m, 1, 0, st);
+        for (int w = 0; w < 2; ++w) run_plan(P, x, nvec, y, nvec, nvec, m, 1, 0, st);
         cudaEventRecord(e0, st);
-        for (int k = 0; k < reps; ++k) run_plan(P, x, 1, y, 1, 1, m, 1, 0, st);
+        for (int k = 0; k < reps; ++k) run_plan(P, x, nvec, y, nvec, nvec, m, 1, 0, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
             ms /= (float)reps;
@@ -346,9 +346,18 @@ static ffspmv_status ensure_multi(ffspmv_t h, bool transpose, int nv, const Plan
             delete np;
             return st;
         }
+        // kept only where a pass over nv vectors beats nv one-vector passes
+        // (measured once, here): wider x words and row sums shrink the panels
+        // and row groups, and on matrices with few entries per column of a
+        // CTA the extra stages cost more than the shared entry stream saves
+        if (st == FFSPMV_OK && np->panel.on && !(h->opt.test_hooks & 4)) {
+            const float tm = time_whole_plan(*np, h->m, nv);
+            const float t1 = time_whole_plan(transpose ? h->AT : h->A, h->m, nv);
+            if (!(tm > 0.0f && t1 > 0.0f && tm < 0.97f * t1)) st = FFSPMV_ERR_UNSUPPORTED;
+        }
         if (st != FFSPMV_OK) {
             free_plan(*np);
-            *np = Plan();  // no such layout: remembered as a plan without panels
+            *np = Plan();  // no such layout, or not faster: remembered as a plan without panels
         }
         mp = np;
     }

@@ -156,12 +156,30 @@ def test_panel_multi_vector_passes(lib, m, pm):
     Widths 2 to 16 cover contiguous blocks (ldx = pass width), strided ones
     (vector loads and scalar loads of x), and remainders of 2 and 1."""
     A = gen.powerlaw_matrix(seed=17, n=60_007, lmax=4000, m=m, pm_fraction=pm)
-    M = make(lib, A, "PANEL", use_pm1=1 if pm else 0)
+    # test hook 4: the wide passes are taken whether or not they are faster
+    M = make(lib, A, "PANEL", use_pm1=1 if pm else 0, test_hooks=4)
     for nvec in (2, 3, 4, 6, 7, 16):
         check_apply(lib, M, A, nvec=nvec, alpha=5 % m, beta=(m - 2) % m, seed=nvec)
         check_apply(lib, M, A, nvec=nvec, transpose=True, seed=nvec + 50)
     width = 4 if m <= 65536 else 2
     assert M.launches(False, 16) == 16 // width     # one launch per pass
+
+
+def test_panel_wide_passes_kept_only_when_faster(lib):
+    """Without the test hook a block on the 1M power-law matrix (few entries
+    per column of a CTA) keeps one-vector passes if the timed 2-vector pass
+    is not faster; either way the products are exact."""
+    A = gen.powerlaw_matrix(seed=1002, m=65521)
+    M = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE)
+    n = M.launches(False, 2)
+    assert n in (1, 2)
+    x = rand_block(5, A.ncols, 2, A.modulus)
+    got = to_host(M.apply(to_dev(x)))
+    rows = np.random.default_rng(5).integers(0, A.nrows, 2000)
+    for r in rows:
+        a, b = A.row_ptr[r], A.row_ptr[r + 1]
+        want = (A.val[a:b].astype(object) @ x[A.col[a:b]].astype(object)) % A.modulus
+        assert list(got[r]) == [int(w) for w in want], r
 
 
 def test_panel_staging_launch_when_groups_exceed_resident(lib):
@@ -172,7 +190,7 @@ def test_panel_staging_launch_when_groups_exceed_resident(lib):
     n = 1_200_000
     for m, q, nvec in ((2**31 - 1, 4, 1), (65521, 2, 4)):
         A = gen.uniform_matrix(9, n, 200_000, np.full(n, 3), m, pm_fraction=0.2)
-        M = make(lib, A, "PANEL", panel_cluster=q, transpose_mode=lib.TRANSPOSE.NONE)
+        M = make(lib, A, "PANEL", panel_cluster=q, transpose_mode=lib.TRANSPOSE.NONE, test_hooks=4)
         assert M.launches(False, nvec) == 2, M.describe()
         check_apply(lib, M, A, nvec=nvec, alpha=3, beta=7, seed=q)
 
@@ -190,7 +208,7 @@ def test_panel_longest_rows_worst_values(lib, use_pm1):
     col = np.concatenate([np.arange(L) * 2 for L in lengths]).astype(np.int32)
     A = gen.CSR(n, nc, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col,
                 np.full(lengths.sum(), m - 1, dtype=np.uint32), m)
-    M = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE, use_pm1=use_pm1)
+    M = make(lib, A, "PANEL", transpose_mode=lib.TRANSPOSE.NONE, use_pm1=use_pm1, test_hooks=4)
     assert "panels:" in M.describe()
     xv = 0 if use_pm1 else m - 1
     x = np.full(nc, xv, dtype=np.uint32)
