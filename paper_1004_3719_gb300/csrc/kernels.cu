@@ -865,101 +865,178 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 // more warps than blocks
                 const u32 w0 = ((u32)warp + kWarps - (s * rot) % kWarps) % kWarps;
                 for (u32 lb = w0 * 32u; lb < nl; lb += 32u * kWarps) {
-                    const u32 tl = lb + lane, c = min(32u, nl - lb);
-                    const bool valid = tl < nl, general = tl < nlg;
-                    u32 e[8], v[8];
-                    XW xw[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        e[u] = 0;
-                        v[u] = 0;
-                        xw[u] = XW{};
-                    }
-                    if (valid) {
-                        // entries of lane j of this 32-lane block: 4j..4j+3 and 4c+4j..4c+4j+3
-                        const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * lane));
-                        const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * c + 4 * lane));
-                        e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
-                        e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
-                        if (general) {
-                            if (SMALL) {
-                                const uint4 w = *reinterpret_cast<const uint4 *>(vb + 2 * 8 * tl);
-                                v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
-                                v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
-                            } else {
-                                const u32 cg = min(32u, nlg - lb);
-                                const uint4 w0 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * lane));
-                                const uint4 w1 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * cg + 4 * lane));
-                                v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
-                                v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
-                            }
+                    if constexpr (NV == 1) {
+                    // one vector: terms and sums per lane value as u32 (m <= 2^16) or u64
+                        const u32 tl = lb + lane, c = min(32u, nl - lb);
+                        const bool valid = tl < nl, general = tl < nlg;
+                        u32 e[8];
+                        AT tm[8];
+    #pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            e[u] = 0;
+                            tm[u] = 0;
                         }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            xw[u] = *reinterpret_cast<const XW *>(xs + (e[u] & kPanelIdxMask) * sizeof(XW));
-                    }
-                    const bool pack = valid && (general ? tl < lpg : tl - nlg < lpp);
-                    // packs sit in lanes [0, lpg) and [nlg, nlg + lpp): a warp-uniform test
-                    const bool packwarp = lb < lpg || (lb + 32u > nlg && lb < nlg + lpp);
-                    // segmented warp sum over the lanes of one row, then one atomic.
-                    // Packs of one row are adjacent within each section; a row
-                    // can have packs in both sections, so the +-1 packs get keys
-                    // of their own (the runs the sum joins must be contiguous).
-                    // Bit i of seg: the lane 2^i further on is in the same run
-                    u32 seg = 0;
-                    bool head = false;
-                    if (packwarp) {
-                        const u32 key = pack ? ((e[0] >> 16) | (general ? 0u : 0x20000u)) : (0x10000u + (u32)lane);
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) {
-                            const u32 k2 = __shfl_down_sync(0xffffffffu, key, 1 << i);
-                            if (lane + (1 << i) < 32 && k2 == key) seg |= 1u << i;
-                        }
-                        const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
-                        head = pack && (lane == 0 || kp != key);
-                    }
-#pragma unroll
-                    for (int k = 0; k < NV; k += VG) {
-                        LT tm[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) tm[u] = 0;
                         if (valid) {
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                LT tv = 0;
-#pragma unroll
-                                for (int h = 0; h < VG; ++h) {
-                                    const u32 xv = XC::get(xw[u], k + h);
-                                    // +-1 sections (Sec. 2.4.2): x or m - x, no value
-                                    const LT t1 = general ? (SMALL ? (LT)red32_lazy(v[u] * xv, M.m, mu32)
-                                                                   : (LT)red64((u64)v[u] * xv, M))
-                                                          : (LT)((e[u] & kPanelNeg) ? M.m - xv : xv);
-                                    tv |= t1 << (32 * h);
+                            // entries of lane j of this 32-lane block: 4j..4j+3 and 4c+4j..4c+4j+3
+                            const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * lane));
+                            const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * c + 4 * lane));
+                            e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
+                            e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
+                            if (general) {
+                                u32 v[8];
+                                if (SMALL) {
+                                    const uint4 w = *reinterpret_cast<const uint4 *>(vb + 2 * 8 * tl);
+                                    v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
+                                    v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
+                                } else {
+                                    const u32 cg = min(32u, nlg - lb);
+                                    const uint4 w0 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * lane));
+                                    const uint4 w1 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * cg + 4 * lane));
+                                    v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
+                                    v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
                                 }
-                                tm[u] = tv;
+    #pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
+                                    tm[u] = SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
+                                }
+                            } else {
+                                // +-1 sections (Sec. 2.4.2): x or m - x, no value
+    #pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
+                                    tm[u] = (AT)((e[u] & kPanelNeg) ? M.m - xv : xv);
+                                }
                             }
                         }
-                        if (k == 0 && lb + 32u * kWarps >= nl) {
-                            // the warp's last lanes of this stage are in registers (the
-                            // terms above read every loaded word): the buffer can be
-                            // refilled while the sums go on
+                        // the warp's last lanes of this stage are in registers (the terms
+                        // above read every loaded word): the buffer can be refilled
+                        // while the sums go on
+                        if (lb + 32u * kWarps >= nl) {
                             __syncwarp();
                             if (lane == 0) mbar_arrive(empty0 + 8u * b);
                             released = true;
                         }
-                        if (packwarp) {
-                            LT sum = 0;
+                        const bool pack = valid && (general ? tl < lpg : tl - nlg < lpp);
+                        // packs sit in lanes [0, lpg) and [nlg, nlg + lpp): a warp-uniform test
+                        if (lb < lpg || (lb + 32u > nlg && lb < nlg + lpp)) {
+                            // segmented warp sum over the lanes of one row, then one atomic.
+                            // Packs of one row are adjacent within each section; a row
+                            // can have packs in both sections, so the +-1 packs get keys
+                            // of their own (the runs the sum joins must be contiguous)
+                            AT sum = 0;
                             if (pack) sum = ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7]));
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) {
-                                const LT o = __shfl_down_sync(0xffffffffu, sum, 1 << i);
-                                if (seg & (1u << i)) sum += o;
+                            const u32 key = pack ? ((e[0] >> 16) | (general ? 0u : 0x20000u)) : (0x10000u + (u32)lane);
+    #pragma unroll
+                            for (int d = 1; d < 32; d <<= 1) {
+                                const AT o = __shfl_down_sync(0xffffffffu, sum, d);
+                                const u32 k2 = __shfl_down_sync(0xffffffffu, key, d);
+                                if (lane + d < 32 && k2 == key) sum += o;
                             }
-                            if (head) atomicAdd(reinterpret_cast<LT *>(acc + (e[0] >> 16) * NV + k), sum);
+                            const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
+                            if (pack && (lane == 0 || kp != key)) atomicAdd(acc + (key & 0xffffu), sum);
                         }
                         if (valid && !pack) {
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) atomicAdd(reinterpret_cast<LT *>(acc + (e[u] >> 16) * NV + k), tm[u]);
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> 16), tm[u]);
+                        }
+                    } else {
+                        const u32 tl = lb + lane, c = min(32u, nl - lb);
+                        const bool valid = tl < nl, general = tl < nlg;
+                        u32 e[8], v[8];
+                        XW xw[8];
+    #pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            e[u] = 0;
+                            v[u] = 0;
+                            xw[u] = XW{};
+                        }
+                        if (valid) {
+                            // entries of lane j of this 32-lane block: 4j..4j+3 and 4c+4j..4c+4j+3
+                            const uint4 e0 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * lane));
+                            const uint4 e1 = *reinterpret_cast<const uint4 *>(sb + 4 * (8 * lb + 4 * c + 4 * lane));
+                            e[0] = e0.x; e[1] = e0.y; e[2] = e0.z; e[3] = e0.w;
+                            e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
+                            if (general) {
+                                if (SMALL) {
+                                    const uint4 w = *reinterpret_cast<const uint4 *>(vb + 2 * 8 * tl);
+                                    v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
+                                    v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
+                                } else {
+                                    const u32 cg = min(32u, nlg - lb);
+                                    const uint4 w0 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * lane));
+                                    const uint4 w1 = *reinterpret_cast<const uint4 *>(vb + 4 * (8 * lb + 4 * cg + 4 * lane));
+                                    v[0] = w0.x; v[1] = w0.y; v[2] = w0.z; v[3] = w0.w;
+                                    v[4] = w1.x; v[5] = w1.y; v[6] = w1.z; v[7] = w1.w;
+                                }
+                            }
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                xw[u] = *reinterpret_cast<const XW *>(xs + (e[u] & kPanelIdxMask) * sizeof(XW));
+                        }
+                        const bool pack = valid && (general ? tl < lpg : tl - nlg < lpp);
+                        // packs sit in lanes [0, lpg) and [nlg, nlg + lpp): a warp-uniform test
+                        const bool packwarp = lb < lpg || (lb + 32u > nlg && lb < nlg + lpp);
+                        // segmented warp sum over the lanes of one row, then one atomic.
+                        // Packs of one row are adjacent within each section; a row
+                        // can have packs in both sections, so the +-1 packs get keys
+                        // of their own (the runs the sum joins must be contiguous).
+                        // Bit i of seg: the lane 2^i further on is in the same run
+                        u32 seg = 0;
+                        bool head = false;
+                        if (packwarp) {
+                            const u32 key = pack ? ((e[0] >> 16) | (general ? 0u : 0x20000u)) : (0x10000u + (u32)lane);
+    #pragma unroll
+                            for (int i = 0; i < 5; ++i) {
+                                const u32 k2 = __shfl_down_sync(0xffffffffu, key, 1 << i);
+                                if (lane + (1 << i) < 32 && k2 == key) seg |= 1u << i;
+                            }
+                            const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
+                            head = pack && (lane == 0 || kp != key);
+                        }
+    #pragma unroll
+                        for (int k = 0; k < NV; k += VG) {
+                            LT tm[8];
+    #pragma unroll
+                            for (int u = 0; u < 8; ++u) tm[u] = 0;
+                            if (valid) {
+    #pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    LT tv = 0;
+    #pragma unroll
+                                    for (int h = 0; h < VG; ++h) {
+                                        const u32 xv = XC::get(xw[u], k + h);
+                                        // +-1 sections (Sec. 2.4.2): x or m - x, no value
+                                        const LT t1 = general ? (SMALL ? (LT)red32_lazy(v[u] * xv, M.m, mu32)
+                                                                       : (LT)red64((u64)v[u] * xv, M))
+                                                              : (LT)((e[u] & kPanelNeg) ? M.m - xv : xv);
+                                        tv |= t1 << (32 * h);
+                                    }
+                                    tm[u] = tv;
+                                }
+                            }
+                            if (k == 0 && lb + 32u * kWarps >= nl) {
+                                // the warp's last lanes of this stage are in registers (the
+                                // terms above read every loaded word): the buffer can be
+                                // refilled while the sums go on
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(empty0 + 8u * b);
+                                released = true;
+                            }
+                            if (packwarp) {
+                                LT sum = 0;
+                                if (pack) sum = ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7]));
+    #pragma unroll
+                                for (int i = 0; i < 5; ++i) {
+                                    const LT o = __shfl_down_sync(0xffffffffu, sum, 1 << i);
+                                    if (seg & (1u << i)) sum += o;
+                                }
+                                if (head) atomicAdd(reinterpret_cast<LT *>(acc + (e[0] >> 16) * NV + k), sum);
+                            }
+                            if (valid && !pack) {
+    #pragma unroll
+                                for (int u = 0; u < 8; ++u) atomicAdd(reinterpret_cast<LT *>(acc + (e[u] >> 16) * NV + k), tm[u]);
+                            }
                         }
                     }
                 }
