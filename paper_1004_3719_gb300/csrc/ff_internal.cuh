@@ -213,7 +213,7 @@ constexpr u32 kPanelNewX = 8u;                // PanelStage::xs: the panel is co
 static_assert(16 * kPanelStages + 8 <= kPanelBarBytes && kPanelStages <= 7,
               "full and empty mbarriers of the stage buffers, the epilogue's receive mbarrier, x slots");
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
-constexpr unsigned kPanelGridSpin = 1u << 20; // polls of an x slice's count before giving up
+constexpr unsigned kPanelGridSpin = 1u << 20; // polls of the grid barrier before giving up
 constexpr u32 kPanelIdxMask = 0x7fffu;        // x element of the panel
 constexpr u32 kPanelNeg = 0x8000u;            // a -1 entry (+-1 sections)
 constexpr long long kPanelLong = 32768;       // longer rows go to split CSR segments
@@ -254,7 +254,7 @@ struct PanelPart {
     const u32 *ent = nullptr;
     const void *val = nullptr;
     void *xh = nullptr;  // u16 / u32 copy of nv x columns, interleaved by vector, zero padded
-    u32 *xflag = nullptr; // [ngroup * q]: launches whose x slice c is staged (fused plans)
+    u32 *gbar = nullptr; // grid barrier: arrivals, generation
 };
 
 // Most clusters of q CTAs of the panel kernel for nv vectors per pass

@@ -695,7 +695,7 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     unsigned char *ebuf = panel_smem + kPanelStages * PX;
     unsigned char *bars = ebuf + kPanelStages * EB;
     uint4 *desc = reinterpret_cast<uint4 *>(bars + kPanelBarBytes);  // (entries, general, packs, x slot)
-    u32 &s_gen = *reinterpret_cast<u32 *>(bars + kPanelBarBytes + 16 * kPanelStages);  // x slices: this launch's count
+    u32 &s_gen = *reinterpret_cast<u32 *>(bars + kPanelBarBytes + 16 * kPanelStages);  // grid barrier generation
     AT *acc = reinterpret_cast<AT *>(bars + kPanelBarBytes + kPanelDescBytes);
     const int q = P.q;
     const int cta = blockIdx.x, g = cta / q, rank = cta % q;
@@ -705,16 +705,16 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     const u32 full0 = (u32)__cvta_generic_to_shared(bars), empty0 = full0 + 8u * kPanelStages;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
-    // x is staged in slices, one per CTA; xflag[c] counts the launches whose
-    // slice c is staged.  Only CTA c writes it, so its own count before this
-    // launch is every slice's (read early: the load overlaps the conversion)
-    const long long xsl = ((P.ncols + (long long)gridDim.x - 1) / gridDim.x + 7) / 8 * 8;  // columns per slice
+    // the grid barrier's generation before this CTA arrives (read early: the
+    // load overlaps the conversion below)
     u32 g0 = 0;
-    if (fused && t == 0) g0 = *reinterpret_cast<volatile const u32 *>(P.xflag + cta);
+    if (fused && t == 0) g0 = ld_acquire_gpu(P.gbar + 1);
     if (fused) {
-        // this CTA's slice of x, converted into the staged copy that every
+        // this CTA's share of x, converted into the staged copy that every
         // CTA's bulk copies read
-        const long long lo = min(P.ncols, (long long)cta * xsl) * NV, hi = min(P.ncols, lo / NV + xsl) * NV;
+        const long long G = gridDim.x;
+        const long long share = ((P.ncols + G - 1) / G + 7) / 8 * 8;
+        const long long lo = min(P.ncols, (long long)cta * share) * NV, hi = min(P.ncols, lo / NV + share) * NV;
         XT *xh = reinterpret_cast<XT *>(P.xh);
         long long done = lo;  // lo, hi: elements of the interleaved copy
         if (ldx == NV && ((uintptr_t)x & 15u) == 0) {
@@ -761,17 +761,22 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     for (u32 r = t; r < nr * NV; r += kPanelThreads) acc[r] = 0;
     __syncthreads();
     if (t == 0) {
-        if (fused) {
-            // the slice is staged: its release covers the CTA's conversion
-            // stores (ordered before it by the barrier above)
-            s_gen = g0 + 1;
-            st_release_gpu(P.xflag + cta, g0 + 1);
-        }
         for (int b = 0; b < kPanelStages; ++b) {
             mbar_init(full0 + 8u * b, 1);
             mbar_init(empty0 + 8u * b, kWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::: "memory");
+        if (fused) {
+            // grid barrier: arrivals in gbar[0], generation in gbar[1]; the
+            // last CTA to arrive resets the count and moves the generation on.
+            // The release of the arrival covers the CTA's conversion stores
+            // (ordered before it by the barrier above)
+            s_gen = g0;
+            if (atom_add_release_gpu(P.gbar, 1u) == gridDim.x - 1) {
+                atomicExch(P.gbar, 0u);
+                st_release_gpu(P.gbar + 1, g0 + 1);
+            }
+        }
     }
     __syncthreads();
     bool timed_out = false;
@@ -779,20 +784,17 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         // Copy warps.  Warp kWarps + b fills stage buffer b: stages b,
         // b + kPanelStages, ...  A thread's bulk copies complete one after
         // another, so each stage's copies come from two threads: lane 1 copies
-        // the entries and values (they do not depend on x, so the first ones
-        // start before x is staged) after adding their bytes to the stage's
-        // full barrier; lane 0, once the panel's slices of x are staged,
-        // publishes the stage descriptor, arrives with the x panel's bytes and
-        // copies the panel.  The warp's first panel waits for its own slices,
-        // its second for every slice; later panels need no check.
+        // the entries and values (they do not depend on x, so the first one
+        // starts before the grid barrier) after adding their bytes to the
+        // stage's full barrier; lane 0, once x is staged, publishes the stage
+        // descriptor, arrives with the x panel's bytes and copies the panel.
         const u32 b = (u32)(warp - kWarps);
         const u32 bar = full0 + 8u * b, ebar = empty0 + 8u * b;
         const u32 d = sbase + kPanelStages * PX + b * EB;
         const unsigned char *xh = reinterpret_cast<const unsigned char *>(P.xh);
         const unsigned char *ev = reinterpret_cast<const unsigned char *>(P.ent);
         const unsigned char *vv = reinterpret_cast<const unsigned char *>(P.val);
-        int xstate = fused ? 0 : 2;  // slices known staged: 0 none, 1 the first panel's, 2 all
-        const u32 want = s_gen;
+        bool xready = !fused;
         for (u32 s = b; s < ns; s += kPanelStages) {
             const PanelStage a = P.stage[s0 + s];
             if (s >= kPanelStages) {
@@ -812,32 +814,19 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
                 if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, a.ngen * (u32)VB, bar);
             }
-            const bool newx = (a.xs & kPanelNewX) != 0;
-            if (newx && xstate < 2) {
-                // the lanes poll the slices this panel (or, the second time,
-                // any panel) reads, 32 at a time
-                const u32 nsl = gridDim.x;
-                u32 lo = 0, hi = nsl - 1;
-                if (xstate == 0) {
-                    const long long c1 = min(P.ncols, (long long)a.xoff + PX / (long long)sizeof(XW)) - 1;
-                    lo = min((u32)((long long)a.xoff / xsl), nsl - 1);
-                    hi = min((u32)(max(c1, 0LL) / xsl), nsl - 1);
-                }
-                bool ok = true;
-                for (u32 c = lo + lane; c <= hi; c += 32) {
+            if (lane == 0) {
+                if (!xready) {
+                    // every CTA's share of x is staged before the first panel copy
                     unsigned spin = 0;
-                    while (ld_acquire_gpu(P.xflag + c) != want)
-                        if (timed_out || ++spin >= kPanelGridSpin) {
-                            ok = false;
+                    while (ld_acquire_gpu(P.gbar + 1) == s_gen)
+                        if (++spin >= kPanelGridSpin) {
+                            timed_out = true;
                             break;
                         }
-                    if (!ok) break;
+                    fence_proxy_async_global();
+                    xready = true;
                 }
-                if (!__all_sync(0xffffffffu, ok)) timed_out = true;
-                xstate = (xstate == 0 && !(lo == 0 && hi == nsl - 1)) ? 1 : 2;
-            }
-            if (lane == 0) {
-                if (newx) fence_proxy_async_global();  // the acquired slices, before the async-proxy copy
+                const bool newx = (a.xs & kPanelNewX) != 0;
                 desc[b] = make_uint4(a.nent, a.ngen, a.npg | (a.npp << 16), a.xs & kPanelSlotMask);  // published by the arrive
                 mbar_expect_tx(bar, newx ? (u32)PX : 0u);
                 if (newx) bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX, xh + (size_t)a.xoff * sizeof(XW), (u32)PX, bar);

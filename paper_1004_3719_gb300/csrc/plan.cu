@@ -680,7 +680,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, int nv, 
     o_val = B.putv(vbytes);
     std::vector<unsigned char> z((size_t)(A.ncols + H.pcols + 64) * xb * H.nv, 0);
     o_xh = B.putv(z);
-    std::vector<u32> bar((size_t)H.ngroup * H.q, 0);  // per-CTA x slice counts
+    std::vector<u32> bar(2, 0);  // grid barrier: arrivals, generation
     o_bar = B.putv(bar);
     return true;
 }
@@ -917,7 +917,7 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
         P.panel.ent = (const u32 *)(base + o_ent);
         P.panel.val = base + o_val;
         P.panel.xh = base + o_xh;
-        P.panel.xflag = (u32 *)(base + o_bar);
+        P.panel.gbar = (u32 *)(base + o_bar);
         describe(P, name);
         char buf[400];
         snprintf(buf, sizeof buf,
