@@ -8,7 +8,7 @@
 // M-Basis leaf.  An order-d problem (d <= 32) runs on one cluster of CTAs
 // that keep, column by column, the residual R = P F (coefficients k..d-1,
 // m x n) and the basis P (coefficients 0..k, m x m) in shared memory.  At
-// order k one warp eliminates the m x n matrix R_k column by column (rows
+// order k four warps eliminate the m x n matrix R_k column by column (rows
 // ordered by (delta_i, i), pivot = the first non-pivot row nonzero in the
 // column), one lane per row; every CTA then applies the same row operations
 // to its coefficients of R and P, one warp per (coefficient, column)
@@ -35,6 +35,7 @@ constexpr int kSbMaxBase = 32;              // largest leaf order
 constexpr int kSbThreads = 512;
 constexpr int kSbWarps = kSbThreads / 32;
 constexpr int kSbCluster = 8;               // CTAs of one leaf (portable cluster size)
+constexpr int kSbElimWarps = 4;             // warps of the leader that eliminate R_k
 constexpr size_t kSbSmemMax = 227 * 1024;
 constexpr size_t kSbAlign = 256;
 constexpr int kSbMaxShift = 1 << 24;
@@ -129,11 +130,12 @@ __device__ __forceinline__ u32 sb_cluster_size()
 
 // One M-Basis leaf on a cluster of C CTAs (C = min(8, n + m)).  Each CTA
 // keeps its columns of [R | P] in shared memory; per order k:
-//   1. the leader's warp 0 eliminates R_k (gathered in the leader), one lane
-//      per row, and sends the operations to every CTA;
+//   1. four warps of the leader eliminate R_k (gathered in the leader), one
+//      lane per row, the columns split between them, and send the
+//      operations to every CTA;
 //   2. every CTA applies them to its positions, one warp per (coefficient,
-//      column) position and one lane per row (R: coefficients k..d-1, P:
-//      0..k);
+//      column) position (two at a time) and one lane per row (R:
+//      coefficients k..d-1, P: 0..k);
 //   3. the pivot rows of each column move up one coefficient (times x), and
 //      the owners of R's columns send R_{k+1} to the leader.
 // Two cluster barriers per order order these steps.
@@ -177,9 +179,12 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
     for (int k = 0; k < d; ++k) {
         SbOps &O = ops[k & 1];
         sb_cluster_sync();   // R_k is complete in the leader
-        if (rank == 0 && warp == 0) {
+        if (rank == 0 && warp < kSbElimWarps) {
             // rows ordered by (delta_i, i); the pivot of column j is the first
-            // row in that order, not yet a pivot, nonzero in the column
+            // row in that order, not yet a pivot, nonzero in the column.  The
+            // elimination warps each hold one row per lane and update the
+            // columns c = warp (mod kSbElimWarps); every one of them finds the
+            // same pivots, and a named barrier ends each column
             const bool row = lane < m;
             int myrank = 0;
 #pragma unroll
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
                 const int dj = __shfl_sync(0xffffffffu, dl, j);
                 myrank += (j < m && (dj < dl || (dj == dl && j < lane))) ? 1 : 0;
             }
-            u32 *Rrow = Rk + lane * kSbRkLd;
+            u32 *__restrict__ Rrow = Rk + lane * kSbRkLd;
             u32 piv = 0u;   // bit r: row r is a pivot at this order
             for (int j = 0; j < n; ++j) {
                 const u32 x = row ? Rrow[j] : 0u;
@@ -195,64 +200,90 @@ __global__ void __launch_bounds__(kSbThreads, 1) k_sb_mbasis(const __grid_consta
                 const u32 key = cand ? (u32)myrank : 64u;
                 const u32 mn = __reduce_min_sync(0xffffffffu, key);
                 uint2 myop = make_uint2(1u, 0u);
-                if (mn == 64u) {   // column j is already zero in every non-pivot row
-                    if (lane == 0) O.piv[j] = -1;
-                } else {
+                if (mn != 64u) {
                     const int q = __ffs(__ballot_sync(0xffffffffu, key == mn)) - 1;
                     const u32 av = __shfl_sync(0xffffffffu, x, q);
                     if (cand && lane != q) {
-                        // row <- av row - x pivot row (fraction free)
+                        // row <- av row - x pivot row (fraction free); columns
+                        // of this warp, their loads issued before the stores
                         const u32 g = p - x;
-                        const u32 *Rq = Rk + q * kSbRkLd;
-                        for (int c = j + 1; c < n; ++c) Rrow[c] = red64((u64)av * Rrow[c] + (u64)g * Rq[c], a.M);
-                        Rrow[j] = 0u;
+                        const u32 *__restrict__ Rq = Rk + q * kSbRkLd;
+                        const int c0 = j + 1 + ((warp - (j + 1)) % kSbElimWarps + kSbElimWarps) % kSbElimWarps;
+                        for (int cb = c0; cb < n; cb += 4 * kSbElimWarps) {
+                            u32 ra[4], qa[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int c = cb + u * kSbElimWarps;
+                                ra[u] = c < n ? Rrow[c] : 0u;
+                                qa[u] = c < n ? Rq[c] : 0u;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int c = cb + u * kSbElimWarps;
+                                if (c < n) Rrow[c] = red64((u64)av * ra[u] + (u64)g * qa[u], a.M);
+                            }
+                        }
                         myop = make_uint2(av, g);
-                        cs = red64((u64)cs * av, a.M);
+                        if (warp == 0) cs = red64((u64)cs * av, a.M);
                     }
                     piv |= 1u << q;
-                    if (lane == 0) O.piv[j] = q;
+                    if (warp == 0 && lane == 0) O.piv[j] = q;
+                } else if (warp == 0 && lane == 0) {
+                    O.piv[j] = -1;   // column j is already zero in every non-pivot row
                 }
-                if (row) O.op[j][lane] = myop;
-                __syncwarp();   // the rows written at this column, before the next one reads them
+                if (warp == 0 && row) O.op[j][lane] = myop;
+                asm volatile("bar.sync 1, %0;" ::"n"(kSbElimWarps * 32) : "memory");   // column j done
             }
             if (row) {
                 const int ip = (int)((piv >> lane) & 1u);
-                O.isp[lane] = ip;
+                if (warp == 0) O.isp[lane] = ip;
                 dl += ip;
             }
-            __syncwarp();
-            // the operations to the other CTAs: rows j < n of op[][], then piv and isp
+            asm volatile("bar.sync 1, %0;" ::"n"(kSbElimWarps * 32) : "memory");   // the operations are complete
+            // the operations to the other CTAs (split over the elimination
+            // warps): rows j < n of op[][], then piv and isp
             const uint4 *src = reinterpret_cast<const uint4 *>(&O);
             const uint4 *tail = reinterpret_cast<const uint4 *>(O.piv);
             const int nq = n * (int)(kSbMaxM * sizeof(uint2) / 16);
-            for (u32 rr = 1; rr < C; ++rr) {
+            for (u32 rr = 1 + (u32)warp; rr < C; rr += kSbElimWarps) {
                 for (int e = lane; e < nq; e += 32) sb_st_remote_v4(sb_remote(src + e, rr), src[e]);
                 if (lane < (int)(2 * kSbMaxM * sizeof(int) / 16)) sb_st_remote_v4(sb_remote(tail + lane, rr), tail[lane]);
             }
         }
         sb_cluster_sync();   // the operations of order k are in every CTA
-        // positions: R's coefficients k..d-1 and P's 0..k of this CTA's columns
-        for (int pos = warp;; pos += kSbWarps) {
-            int i = 0, t = pos, w = 0;
-            for (; i < own; ++i) {
-                w = (int)rank + i * (int)C;
+        // positions: R's coefficients k..d-1 and P's 0..k of this CTA's
+        // columns, two per warp at a time (two independent chains of
+        // operations in flight)
+        auto cell_of = [&](int pos) -> u32 * {
+            for (int i = 0; i < own; ++i) {
+                const int w = (int)rank + i * (int)C;
                 const int cnt = w < n ? d - k : k + 1;
-                if (t < cnt) break;
-                t -= cnt;
+                if (pos < cnt) return col + (size_t)i * cst + (size_t)(w < n ? k + pos : pos) * m;
+                pos -= cnt;
             }
-            if (i == own) break;
-            u32 *cell = col + (size_t)i * cst + (size_t)(w < n ? k + t : t) * m;
-            u32 v = lane < m ? cell[lane] : 0u;
+            return nullptr;
+        };
+        for (int pos = warp;; pos += 2 * kSbWarps) {
+            u32 *c0 = cell_of(pos);
+            if (!c0) break;
+            u32 *c1 = cell_of(pos + kSbWarps);
+            u32 v0 = lane < m ? c0[lane] : 0u, v1 = (c1 && lane < m) ? c1[lane] : 0u;
             for (int j = 0; j < n; ++j) {
                 const int q = O.piv[j];
                 if (q < 0) continue;
-                const u32 vq = __shfl_sync(0xffffffffu, v, q);
+                const u32 q0 = __shfl_sync(0xffffffffu, v0, q), q1 = __shfl_sync(0xffffffffu, v1, q);
                 if (lane < m) {
                     const uint2 op = O.op[j][lane];
-                    if (op.y) v = red64((u64)op.x * v + (u64)op.y * vq, a.M);
+                    if (op.y) {
+                        v0 = red64((u64)op.x * v0 + (u64)op.y * q0, a.M);
+                        v1 = red64((u64)op.x * v1 + (u64)op.y * q1, a.M);
+                    }
                 }
             }
-            if (lane < m) cell[lane] = v;
+            if (lane < m) {
+                c0[lane] = v0;
+                if (c1) c1[lane] = v1;
+            }
         }
         __syncthreads();
         // pivot rows times x: R's coefficients k..d-1 and P's 0..k+1 move up by one
