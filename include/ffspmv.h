@@ -98,7 +98,8 @@ typedef struct {
                                   bit 1 = the x-panel kernel never issues the copies of the second
                                   stage of each CTA, so the waits for it run out (the status word
                                   read by spmv_check_status); bit 2 = x-panel blocks always take
-                                  the 2- and 4-vector passes, without the timing that decides it */
+                                  the 2- and 4-vector passes, without the timing that decides it;
+                                  bit 3 = x-panel blocks never take them (one-vector passes) */
     int32_t panel_cluster;     /* x-panel layout: CTAs per cluster (column groups); 0 = chosen by
                                   the builder, 1, 2 or 4 to force one */
 } ffspmv_options;

@@ -401,7 +401,7 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     // x-panel blocks: passes of 4 or 2 vectors read the matrix once for all
     // of them (Sec. 2.5.1), on layouts built for that width
     for (int c0 = 0; c0 < nvec;) {
-        int nv = pass_width(*P, nvec - c0);
+        int nv = (h->opt.test_hooks & 8) ? 1 : pass_width(*P, nvec - c0);
         const Plan *Q = P;
         if (nv > 1) {
             ffspmv_status s = ensure_multi(h, transpose, nv, &Q);
@@ -499,7 +499,7 @@ ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec, i
             n += count_plan_launches(P, nvec);
         } else {
             for (int c0 = 0; c0 < nvec;) {
-                int nv = pass_width(P, nvec - c0);
+                int nv = (h->opt.test_hooks & 8) ? 1 : pass_width(P, nvec - c0);
                 const Plan *Q = &P;
                 if (nv > 1) {
                     ffspmv_status s = ensure_multi(h, transpose != 0, nv, &Q);

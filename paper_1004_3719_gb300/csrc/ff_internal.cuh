@@ -253,7 +253,9 @@ struct PanelPart {
     const PanelStage *stage = nullptr;
     const u32 *ent = nullptr;
     const void *val = nullptr;
-    void *xh = nullptr;  // u16 / u32 copy of nv x columns, interleaved by vector, zero padded
+    void *xh = nullptr;  // staged x: u16 / u32, nv vectors interleaved, zero padded; xcols copies
+    long long xstride = 0; // elements from one staged copy to the next
+    int xcols = 1;         // staged copies (vectors staged by one launch when nv = 1)
     u32 *gbar = nullptr; // grid barrier: arrivals, generation
 };
 

@@ -675,7 +675,7 @@ struct PanelX {
 template <bool SMALL, int NV>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__restrict__ y, long long ldy,
-        const Mod M, int *status, int skip_stage, int fused)
+        const Mod M, int *status, int skip_stage, int conv)
 {
     typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
@@ -707,6 +707,11 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
 
     // the grid barrier's generation before this CTA arrives (read early: the
     // load overlaps the conversion below)
+    // conv > 0: this launch stages x itself (all its CTAs are resident): conv
+    // staged columns (vectors vcol.. of the block, one launch per group of up
+    // to four; later launches of the group read the staged copy), or one
+    // group of NV interleaved vectors
+    const int fused = conv > 0;
     u32 g0 = 0;
     if (fused && t == 0) g0 = ld_acquire_gpu(P.gbar + 1);
     if (fused) {
@@ -717,7 +722,23 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         const long long lo = min(P.ncols, (long long)cta * share) * NV, hi = min(P.ncols, lo / NV + share) * NV;
         XT *xh = reinterpret_cast<XT *>(P.xh);
         long long done = lo;  // lo, hi: elements of the interleaved copy
-        if (ldx == NV && ((uintptr_t)x & 15u) == 0) {
+        if (NV == 1 && conv > 1) {
+            // conv vectors at once, one staged column each (P.xstride apart)
+            const bool vec = conv == 4 && ldx % 4 == 0 && ((uintptr_t)x & 15u) == 0;
+            for (long long i = lo + t; i < hi; i += kPanelThreads) {
+                u32 c[4];
+                if (vec) {
+                    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(x + i * ldx));
+                    c[0] = w.x; c[1] = w.y; c[2] = w.z; c[3] = w.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) c[k] = k < conv ? __ldg(x + i * ldx + k) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < conv) xh[k * P.xstride + i] = (XT)c[k];
+            }
+        } else if (ldx == NV && ((uintptr_t)x & 15u) == 0) {
             // the NV columns are contiguous: four 16-byte loads in flight per
             // thread before their stores
             const long long i1 = hi / 4;
@@ -1113,11 +1134,16 @@ int panel_max_clusters(bool small, int nv, int q, size_t smem)
 // (one row group per resident cluster); otherwise a staging launch runs first.
 static bool panel_fused(const PanelPart &pp) { return pp.ngroup <= pp.resident; }
 
+// One pass of the panel kernel over vectors vcol.. of the block.  conv: for a
+// plan whose CTAs are all resident, the staged columns this launch converts
+// (0: it reads column xcol that an earlier launch of the group staged).
 static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *y, long long ldy,
-                               int vcol, const Mod &M, cudaStream_t st, const PanelCtl *ctl)
+                               int vcol, int conv, int xcol, const Mod &M, cudaStream_t st, const PanelCtl *ctl)
 {
-    const PanelPart &pp = P.panel;
+    PanelPart pp = P.panel;
     const int fused = panel_fused(pp) ? 1 : 0;
+    if (fused) pp.xh = (char *)pp.xh + (size_t)xcol * pp.xstride * (pp.small ? 2 : 4);
+    else conv = 0;
     if (!fused) {
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
@@ -1151,7 +1177,7 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
     const u32 *xv = x + vcol;
     int *status = ctl ? ctl->status : nullptr;
     const int skip = ctl ? ctl->skip_stage : -1;
-    FF_CUDA(cudaLaunchKernelEx(&cfg, kf, pp, xv, ldx, yv, ldy, M, status, skip, fused));
+    FF_CUDA(cudaLaunchKernelEx(&cfg, kf, pp, xv, ldx, yv, ldy, M, status, skip, conv));
     return FFSPMV_OK;
 }
 
@@ -1183,7 +1209,11 @@ ffspmv_status run_plan(const Plan &P, const u32 *x, long long ldx, u32 *y,
         // in.  A plan for NV vectors per pass takes blocks of a multiple of NV
         if (nvec % P.panel.nv) return FFSPMV_ERR_ARG;
         for (int v = 0; v < nvec; v += P.panel.nv) {
-            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, M1, st, ctl);
+            // one vector per pass: the first launch of each group of
+            // P.panel.xcols vectors stages all of them
+            const int g = P.panel.xcols, k = (v / P.panel.nv) % g;
+            const int conv = k ? 0 : (P.panel.nv == 1 ? std::min(g, nvec - v) : 1);
+            ffspmv_status r = run_panel(P, x, ldx, y, ldy, v, conv, k, M1, st, ctl);
             if (r != FFSPMV_OK) return r;
         }
     }

@@ -678,7 +678,10 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, int nv, 
     o_stage = B.putv(H.stage);
     o_ent = B.putv(H.ent);
     o_val = B.putv(vbytes);
-    std::vector<unsigned char> z((size_t)(A.ncols + H.pcols + 64) * xb * H.nv, 0);
+    // staged x: four copies (one per vector of a group) for one-vector passes
+    pp.xcols = H.nv == 1 ? 4 : 1;
+    pp.xstride = (A.ncols + H.pcols + 64 + 63) / 64 * 64 * H.nv;
+    std::vector<unsigned char> z((size_t)pp.xstride * pp.xcols * xb, 0);
     o_xh = B.putv(z);
     std::vector<u32> bar(2, 0);  // grid barrier: arrivals, generation
     o_bar = B.putv(bar);

@@ -165,6 +165,26 @@ def test_panel_multi_vector_passes(lib, m, pm):
     assert M.launches(False, 16) == 16 // width     # one launch per pass
 
 
+@pytest.mark.parametrize("m", [65521, 2**31 - 1])
+def test_panel_one_vector_passes_stage_groups(lib, m):
+    """One-vector passes over a block (test hook 8): the first launch of each
+    group of four vectors stages all of them (vector loads when ldx is a
+    multiple of four, scalar loads otherwise), the others read the staged
+    copies; groups of 4, 3, 2 and 1 and the staging launch of plans whose
+    row groups exceed the resident clusters."""
+    A = gen.powerlaw_matrix(seed=19, n=50_021, lmax=3000, m=m, pm_fraction=0.2)
+    M = make(lib, A, "PANEL", use_pm1=1, test_hooks=8)
+    for nvec in (2, 3, 4, 5, 7, 16):
+        check_apply(lib, M, A, nvec=nvec, alpha=3, beta=5, seed=40 + nvec)
+        check_apply(lib, M, A, nvec=nvec, transpose=True, seed=60 + nvec)
+    assert M.launches(False, 7) == 7
+    n = 1_200_000
+    B = gen.uniform_matrix(9, n, 200_000, np.full(n, 3), m, pm_fraction=0.2)
+    q = 4 if m > 65536 else 2
+    MB = make(lib, B, "PANEL", panel_cluster=q, transpose_mode=lib.TRANSPOSE.NONE, test_hooks=8)
+    check_apply(lib, MB, B, nvec=6, seed=77)
+
+
 def test_panel_wide_passes_kept_only_when_faster(lib):
     """Without the test hook a block on the 1M power-law matrix (few entries
     per column of a CTA) keeps one-vector passes if the timed 2-vector pass
