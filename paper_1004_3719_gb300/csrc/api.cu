@@ -372,6 +372,27 @@ static int pass_width(const Plan &P, int left)
     return left >= 2 ? 2 : 1;
 }
 
+// The next pass over a block with `left` vectors to go: the widest wide
+// layout that exists and was kept, else the base plan for all `left` vectors
+// (one-vector passes, x staged four vectors at a time).
+static ffspmv_status next_pass(ffspmv_t h, bool transpose, const Plan *P, int left, const Plan **Q, int *nv)
+{
+    *Q = P;
+    *nv = left;
+    if (h->opt.test_hooks & 8) return FFSPMV_OK;
+    for (int w = pass_width(*P, left); w > 1; w /= 2) {
+        const Plan *M = nullptr;
+        ffspmv_status s = ensure_multi(h, transpose, w, &M);
+        if (s != FFSPMV_OK) return s;
+        if (M) {
+            *Q = M;
+            *nv = w;
+            return FFSPMV_OK;
+        }
+    }
+    return FFSPMV_OK;
+}
+
 static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_x,
                                   int64_t ldx, uint32_t *d_y, int64_t ldy,
                                   int32_t nvec, uint32_t alpha, uint32_t beta,
@@ -401,17 +422,11 @@ static ffspmv_status apply_common(ffspmv_t h, bool transpose, const uint32_t *d_
     // x-panel blocks: passes of 4 or 2 vectors read the matrix once for all
     // of them (Sec. 2.5.1), on layouts built for that width
     for (int c0 = 0; c0 < nvec;) {
-        int nv = (h->opt.test_hooks & 8) ? 1 : pass_width(*P, nvec - c0);
         const Plan *Q = P;
-        if (nv > 1) {
-            ffspmv_status s = ensure_multi(h, transpose, nv, &Q);
-            if (s != FFSPMV_OK) return s;
-            if (!Q) {
-                Q = P;
-                nv = 1;
-            }
-        }
-        ffspmv_status s = run_plan(*Q, d_x + c0, ldx, d_y + c0, ldy, nv, h->m, alpha % h->m, beta % h->m, st, &ctl);
+        int nv = 1;
+        ffspmv_status s = next_pass(h, transpose, P, nvec - c0, &Q, &nv);
+        if (s != FFSPMV_OK) return s;
+        s = run_plan(*Q, d_x + c0, ldx, d_y + c0, ldy, nv, h->m, alpha % h->m, beta % h->m, st, &ctl);
         if (s != FFSPMV_OK) return s;
         c0 += nv;
     }
@@ -499,16 +514,10 @@ ffspmv_status spmv_count_launches(ffspmv_t h, int32_t transpose, int32_t nvec, i
             n += count_plan_launches(P, nvec);
         } else {
             for (int c0 = 0; c0 < nvec;) {
-                int nv = (h->opt.test_hooks & 8) ? 1 : pass_width(P, nvec - c0);
                 const Plan *Q = &P;
-                if (nv > 1) {
-                    ffspmv_status s = ensure_multi(h, transpose != 0, nv, &Q);
-                    if (s != FFSPMV_OK) return s;
-                    if (!Q) {
-                        Q = &P;
-                        nv = 1;
-                    }
-                }
+                int nv = 1;
+                ffspmv_status s = next_pass(h, transpose != 0, &P, nvec - c0, &Q, &nv);
+                if (s != FFSPMV_OK) return s;
                 n += count_plan_launches(*Q, nv);
                 c0 += nv;
             }
