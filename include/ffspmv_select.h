@@ -118,10 +118,10 @@ ffspmv_status ffspmv_selector_load(const float *params, int64_t count);
  * 4 CTAs) or FFSPMV_LAYOUT_PANEL (x-panel, the builder's cluster size).  A
  * cluster size is named only when its predicted time beats the other two by
  * FFSPMV_SEL_Q_MARGIN (log ratio), and the network's own table only when it
- * beats the best other layout by FFSPMV_SEL_NET_MARGIN: that output is
- * learned from the exhaustive search's table, which the network's table
- * only approaches.  This is what FFSPMV_SEL_LEARNED builds under
- * FFSPMV_FMT_AUTO. */
+ * beats the heuristic table by FFSPMV_SEL_NET_MARGIN: that output is learned
+ * from the exhaustive search's table, which the network's table only
+ * approaches.  This is what FFSPMV_SEL_LEARNED builds under FFSPMV_FMT_AUTO
+ * (with the timed check of FFSPMV_SEL_VERIFY_MARGIN). */
 enum {
     FFSPMV_LAYOUT_BINNED = 0,
     FFSPMV_LAYOUT_NETBINS = 1,
@@ -132,6 +132,10 @@ enum {
 };
 #define FFSPMV_SEL_Q_MARGIN 0.05f
 #define FFSPMV_SEL_NET_MARGIN 0.15f
+/* FFSPMV_SEL_LEARNED builds and times the best x-panel and the best binned
+ * layout when their predicted times are this close (log ratio), and keeps
+ * the faster */
+#define FFSPMV_SEL_VERIFY_MARGIN 0.15f
 ffspmv_status ffspmv_selector_choose(int64_t nrows, int64_t ncols, int64_t nnz,
                                      const int64_t *row_ptr, const int32_t *col,
                                      const uint32_t *values, uint32_t modulus, int32_t *best,

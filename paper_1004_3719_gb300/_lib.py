@@ -134,6 +134,7 @@ OUT_PANEL = NUM_FORMATS + 2     # whole plan: log(t_panel_q / t_binned), q = 1, 
 MATRIX_INPUT = -1.0             # every bin feature of the matrix-level input
 LAYOUT_BINNED, LAYOUT_NETBINS, LAYOUT_PANEL_Q1, LAYOUT_PANEL_Q2, LAYOUT_PANEL_Q4, LAYOUT_PANEL = range(6)
 SEL_Q_MARGIN, SEL_NET_MARGIN = 0.05, 0.15   # log-ratio margins of the layout rule
+SEL_VERIFY_MARGIN = 0.15                    # closer families are timed (FFSPMV_SEL_VERIFY_MARGIN)
 MLP_PARAMS = (MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN
               + MLP_OUT * MLP_HIDDEN + MLP_OUT)
 SELECTOR_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.npy")

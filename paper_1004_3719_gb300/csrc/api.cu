@@ -140,29 +140,40 @@ ffspmv_status build_with_selector(Plan &P, long long nrows, long long ncols,
     if (o.priority_format == FFSPMV_FMT_AUTO && o.selector == FFSPMV_SEL_LEARNED) {
         // the network's matrix-level outputs choose the layout: the x-panel
         // plan, the binned plan with its own per-bin table, or the binned
-        // plan with the heuristic table (least predicted whole-plan time)
+        // plan with the heuristic table (least predicted whole-plan time);
+        // when the best of the other family is predicted within
+        // FFSPMV_SEL_VERIFY_MARGIN, both are built and the faster is kept
         BinChoice bins[kBins];
-        int layout = -1;
-        ffspmv_status st = choose_bins(o.selector, nrows, ncols, ptr, col, val, m, o, bins, &layout);
+        int layout = -1, alt = -1;
+        ffspmv_status st = choose_bins(o.selector, nrows, ncols, ptr, col, val, m, o, bins, &layout, &alt);
         if (st != FFSPMV_OK) return st;
-        ffspmv_options o2 = o;
         // no network installed: the exhaustive bins, and the panel rule of AUTO
-        const bool panel = layout >= FFSPMV_LAYOUT_PANEL_Q1 || (layout < 0 && panel_preferred(ncols, ptr[nrows], m));
-        if (panel && ptr[nrows] > 0) {
-            o2.priority_format = FFSPMV_FMT_PANEL;
-            if (layout >= FFSPMV_LAYOUT_PANEL_Q1 && layout <= FFSPMV_LAYOUT_PANEL_Q4)
-                o2.panel_cluster = 1 << (layout - FFSPMV_LAYOUT_PANEL_Q1);
+        if (layout < 0) layout = panel_preferred(ncols, ptr[nrows], m) ? FFSPMV_LAYOUT_PANEL : FFSPMV_LAYOUT_NETBINS;
+        auto build_layout = [&](Plan &Q, int lay) -> ffspmv_status {
+            ffspmv_options o2 = o;
+            if (lay >= FFSPMV_LAYOUT_PANEL_Q1 && ptr[nrows] > 0) {
+                o2.priority_format = FFSPMV_FMT_PANEL;
+                if (lay <= FFSPMV_LAYOUT_PANEL_Q4) o2.panel_cluster = 1 << (lay - FFSPMV_LAYOUT_PANEL_Q1);
+                if (build_plan_ex(Q, nrows, ncols, ptr, col, val, m, o2, nullptr) == FFSPMV_OK && Q.panel.on)
+                    return FFSPMV_OK;
+                free_plan(Q);
+                Q = Plan();
+                lay = FFSPMV_LAYOUT_NETBINS;
+                o2.panel_cluster = o.panel_cluster;
+            }
+            o2.priority_format = FFSPMV_FMT_BINNED;
+            return build_plan_ex(Q, nrows, ncols, ptr, col, val, m, o2, lay == FFSPMV_LAYOUT_BINNED ? nullptr : bins);
+        };
+        if ((st = build_layout(P, layout)) != FFSPMV_OK) return st;
+        if (alt >= 0) {
             Plan Q;
-            if (build_plan_ex(Q, nrows, ncols, ptr, col, val, m, o2, nullptr) == FFSPMV_OK && Q.panel.on) {
-                P = Q;
-                return FFSPMV_OK;
+            if (build_layout(Q, alt) == FFSPMV_OK) {
+                const float tp = time_whole_plan(P, m), tq = time_whole_plan(Q, m);
+                if (tq > 0.0f && (tp < 0.0f || tq < tp)) std::swap(P, Q);
             }
             free_plan(Q);
         }
-        o2.priority_format = FFSPMV_FMT_BINNED;
-        o2.panel_cluster = o.panel_cluster;
-        const bool own_table = layout != FFSPMV_LAYOUT_BINNED;
-        return build_plan_ex(P, nrows, ncols, ptr, col, val, m, o2, own_table ? bins : nullptr);
+        return FFSPMV_OK;
     }
     const bool wants_bins = o.priority_format == FFSPMV_FMT_BINNED ||
                             (o.priority_format == FFSPMV_FMT_AUTO &&

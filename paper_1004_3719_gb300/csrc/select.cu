@@ -537,7 +537,7 @@ ffspmv_status tune_bins(long long nrows, long long ncols, const long long *ptr, 
 }
 
 ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, const long long *hptr,
-                              const int *hcol, const u32 *hval, u32 m, int *best, int *layout)
+                              const int *hcol, const u32 *hval, u32 m, int *best, int *layout, int *alt = nullptr)
 {
     std::vector<float> w;
     {
@@ -594,7 +594,10 @@ ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, c
         best[3 * b + 2] = 1;
     }
     if (layout) {
-        // least predicted whole-plan time, relative to the heuristic binned plan (0)
+        // least predicted whole-plan time, relative to the heuristic binned
+        // plan (0), between the two families: x-panel (a cluster size only
+        // past FFSPMV_SEL_Q_MARGIN) and binned (the network's own table only
+        // past FFSPMV_SEL_NET_MARGIN)
         const float *o = &hout[kBins * kOut];
         int kq = 0;
         for (int k = 1; k < 3; ++k)
@@ -602,27 +605,28 @@ ffspmv_status selector_choose(long long nrows, long long ncols, long long nnz, c
         float second = 1e30f;
         for (int k = 0; k < 3; ++k)
             if (k != kq) second = fminf(second, o[FFSPMV_OUT_PANEL + k]);
-        const float tp = o[FFSPMV_OUT_PANEL + kq];
-        *layout = FFSPMV_LAYOUT_BINNED;
-        float bestv = 0.f;
-        if (tp < bestv) {
-            bestv = tp;
-            *layout = second - tp > FFSPMV_SEL_Q_MARGIN ? FFSPMV_LAYOUT_PANEL_Q1 + kq : FFSPMV_LAYOUT_PANEL;
-        }
-        if (o[FFSPMV_OUT_NETBINS] < bestv - FFSPMV_SEL_NET_MARGIN) *layout = FFSPMV_LAYOUT_NETBINS;
+        const float vp = o[FFSPMV_OUT_PANEL + kq];
+        const int lp = second - vp > FFSPMV_SEL_Q_MARGIN ? FFSPMV_LAYOUT_PANEL_Q1 + kq : FFSPMV_LAYOUT_PANEL;
+        const bool net = o[FFSPMV_OUT_NETBINS] < -FFSPMV_SEL_NET_MARGIN;
+        const float vb = net ? o[FFSPMV_OUT_NETBINS] : 0.f;
+        const int lb = net ? FFSPMV_LAYOUT_NETBINS : FFSPMV_LAYOUT_BINNED;
+        *layout = vp < vb ? lp : lb;
+        if (alt) *alt = fabsf(vp - vb) < FFSPMV_SEL_VERIFY_MARGIN ? (vp < vb ? lb : lp) : -1;
     }
     return FFSPMV_OK;
 }
 
 ffspmv_status choose_bins(int selector, long long nrows, long long ncols, const long long *ptr,
                           const int *col, const u32 *val, u32 m, const ffspmv_options &o,
-                          BinChoice *bins, int *layout)
+                          BinChoice *bins, int *layout, int *alt)
 {
     const long long nnz = ptr[nrows];
     std::vector<int> best(3 * kBins, 0);
     ffspmv_status rs = FFSPMV_ERR_UNSUPPORTED;
     if (layout) *layout = -1;
-    if (selector == FFSPMV_SEL_LEARNED) rs = selector_choose(nrows, ncols, nnz, ptr, col, val, m, best.data(), layout);
+    if (alt) *alt = -1;
+    if (selector == FFSPMV_SEL_LEARNED)
+        rs = selector_choose(nrows, ncols, nnz, ptr, col, val, m, best.data(), layout, alt);
     if (rs == FFSPMV_ERR_UNSUPPORTED || selector == FFSPMV_SEL_EXHAUSTIVE) {
         std::vector<float> t(kBins * kFormats), pt(kBins * 2);
         std::vector<long long> sn(kBins);
