@@ -235,6 +235,7 @@ struct PanelStage {
 struct PanelPart {
     bool on = false;
     bool small = true;   // m <= 2^16: u16 x and values, u32 row sums
+    bool tiny = false;   // m <= 256, one vector per pass: u8 x and values, u32 row sums
     int nv = 1;          // vectors per pass: x and row sums interleaved by vector
     int q = 1;           // CTAs per cluster (column groups)
     int ngroup = 0;      // row groups
@@ -262,7 +263,7 @@ struct PanelPart {
 // Most clusters of q CTAs of the panel kernel for nv vectors per pass
 // resident at once with `smem` bytes of dynamic shared memory each (0 when
 // the launch cannot fit).
-int panel_max_clusters(bool small, int nv, int q, size_t smem);
+int panel_max_clusters(bool small, int nv, int q, size_t smem, bool tiny = false);
 
 // One matrix plan (A or A^T).
 struct Plan {

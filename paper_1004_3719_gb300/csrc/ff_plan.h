@@ -46,6 +46,7 @@ bool format_valid(int f, int bin, long long maxlen);
 // entry words and values (u32 here; stored as u16 when m <= 2^16).
 struct PanelHost {
     bool small = true;
+    bool tiny = false;  // m <= 256, one vector per pass: u8 x and values
     int nv = 1;
     int q = 1, ngroup = 0, rows_max = 0, resident = 0, px = 0, pe = 0, eb = 0;
     size_t smem = 0;

@@ -535,7 +535,9 @@ __global__ void __launch_bounds__(256) k_x_stage(const u32 *__restrict__ x, long
         const long long n4 = n / 4;
         for (long long i = t; i < n4; i += nth) {
             const uint4 v = __ldg(reinterpret_cast<const uint4 *>(x) + i);
-            if constexpr (sizeof(XT) == 2) {
+            if constexpr (sizeof(XT) == 1) {
+                reinterpret_cast<u32 *>(xs)[i] = (v.x & 0xffu) | (v.y & 0xffu) << 8 | (v.z & 0xffu) << 16 | v.w << 24;
+            } else if constexpr (sizeof(XT) == 2) {
                 uint2 o;
                 o.x = (v.x & 0xffffu) | (v.y << 16);
                 o.y = (v.z & 0xffffu) | (v.w << 16);
@@ -671,13 +673,16 @@ struct PanelX {
 };
 
 // y = alpha A x + beta y for NV vectors at once (x: columns vcol..vcol+NV-1
-// of the block, interleaved in the staged copy; row sums [row][NV]).
-template <bool SMALL, int NV>
+// of the block, interleaved in the staged copy; row sums [row][NV]).  TINY
+// (m <= 256, NV = 1): x and values as u8, terms v x < 2^16 added unreduced.
+template <bool SMALL, int NV, bool TINY = false>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__restrict__ y, long long ldy,
         const Mod M, int *status, int skip_stage, int conv)
 {
-    typedef typename std::conditional<SMALL, unsigned short, u32>::type XT;
+    static_assert(!TINY || (SMALL && NV == 1), "u8 x: one vector, m <= 256");
+    typedef typename std::conditional<TINY, unsigned char,
+                                      typename std::conditional<SMALL, unsigned short, u32>::type>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
     // a lane's term: one row sum's (AT), or, for 16-bit residues and NV > 1,
     // two vectors' u32 sums side by side in a u64 (each half stays below
@@ -685,9 +690,9 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     typedef typename std::conditional<SMALL && NV == 1, u32, u64>::type LT;
     constexpr int VG = SMALL && NV > 1 ? 2 : 1;  // vectors per term
     typedef PanelX<SMALL, NV> XC;
-    typedef typename XC::W XW;
+    typedef typename std::conditional<TINY, XT, typename XC::W>::type XW;
     static_assert(sizeof(XW) == sizeof(XT) * NV, "x word of a column");
-    constexpr int VB = SMALL ? 2 : 4;
+    constexpr int VB = TINY ? 1 : SMALL ? 2 : 4;
     constexpr int kWarps = kPanelConsumers / 32;
     extern __shared__ __align__(128) unsigned char panel_smem[];
     const int PX = P.px, EB = P.eb;
@@ -751,7 +756,10 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 for (int u = 0; u < 4; ++u) {
                     const long long i = i0 + u * kPanelThreads;
                     if (i >= i1) break;
-                    if constexpr (SMALL) {
+                    if constexpr (TINY) {
+                        reinterpret_cast<u32 *>(xh)[i] =
+                            (v[u].x & 0xffu) | (v[u].y & 0xffu) << 8 | (v[u].z & 0xffu) << 16 | v[u].w << 24;
+                    } else if constexpr (SMALL) {
                         uint2 o;
                         o.x = (v[u].x & 0xffffu) | (v[u].y << 16);
                         o.y = (v[u].z & 0xffffu) | (v[u].w << 16);
@@ -828,12 +836,14 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                 if (!__shfl_sync(0xffffffffu, ok, 0)) timed_out = true;
             }
             if ((int)s == skip_stage) continue;  // testing: this stage is never issued
-            const u32 dbytes = a.nent * 4u + a.ngen * (u32)VB;
+            // values: u8 ones are copied in whole 16-byte blocks (the layout pads them)
+            const u32 vbytes = TINY ? (a.ngen + 15u) & ~15u : a.ngen * (u32)VB;
+            const u32 dbytes = a.nent * 4u + vbytes;
             if (lane == 1) mbar_add_tx(bar, dbytes);
             __syncwarp();  // the bytes are added before lane 0's arrive
             if (lane == 1) {
                 bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
-                if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, a.ngen * (u32)VB, bar);
+                if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, vbytes, bar);
             }
             if (lane == 0) {
                 if (!xready) {
@@ -894,7 +904,14 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                             e[4] = e1.x; e[5] = e1.y; e[6] = e1.z; e[7] = e1.w;
                             if (general) {
                                 u32 v[8];
-                                if (SMALL) {
+                                if (TINY) {
+                                    const uint2 w = *reinterpret_cast<const uint2 *>(vb + 8 * tl);
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        v[u] = (w.x >> (8 * u)) & 0xffu;
+                                        v[u + 4] = (w.y >> (8 * u)) & 0xffu;
+                                    }
+                                } else if (SMALL) {
                                     const uint4 w = *reinterpret_cast<const uint4 *>(vb + 2 * 8 * tl);
                                     v[0] = w.x & 0xffffu; v[1] = w.x >> 16; v[2] = w.y & 0xffffu; v[3] = w.y >> 16;
                                     v[4] = w.z & 0xffffu; v[5] = w.z >> 16; v[6] = w.w & 0xffffu; v[7] = w.w >> 16;
@@ -908,7 +925,8 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     #pragma unroll
                                 for (int u = 0; u < 8; ++u) {
                                     const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
-                                    tm[u] = SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
+                                    tm[u] = TINY ? (AT)(v[u] * xv)
+                                                 : SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
                                 }
                             } else {
                                 // +-1 sections (Sec. 2.4.2): x or m - x, no value
@@ -1100,16 +1118,17 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
 
 // The panel kernel instance for (16-bit residues, vectors per pass).
 typedef void (*PanelKernel)(const PanelPart, const u32 *, long long, u32 *, long long, const Mod, int *, int, int);
-static PanelKernel panel_kernel(bool small, int nv)
+static PanelKernel panel_kernel(bool small, int nv, bool tiny = false)
 {
+    if (tiny) return k_panel<true, 1, true>;
     if (small) return nv == 4 ? k_panel<true, 4> : nv == 2 ? k_panel<true, 2> : k_panel<true, 1>;
     return nv == 2 ? k_panel<false, 2> : k_panel<false, 1>;
 }
 
-int panel_max_clusters(bool small, int nv, int q, size_t smem)
+int panel_max_clusters(bool small, int nv, int q, size_t smem, bool tiny)
 {
     if (!(nv == 1 || nv == 2 || (nv == 4 && small))) return 0;
-    const PanelKernel kf = panel_kernel(small, nv);
+    const PanelKernel kf = panel_kernel(small, nv, tiny && small && nv == 1);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)q, 1, 1);
@@ -1142,7 +1161,7 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
 {
     PanelPart pp = P.panel;
     const int fused = panel_fused(pp) ? 1 : 0;
-    if (fused) pp.xh = (char *)pp.xh + (size_t)xcol * pp.xstride * (pp.small ? 2 : 4);
+    if (fused) pp.xh = (char *)pp.xh + (size_t)xcol * pp.xstride * (pp.tiny ? 1 : pp.small ? 2 : 4);
     else conv = 0;
     if (!fused) {
         int dev = 0, nsm = 0;
@@ -1152,14 +1171,15 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
             (unsigned)std::max<long long>(1, std::min<long long>((P.ncols / 4 + 255) / 256, 8LL * std::max(nsm, 1)));
         unsigned short *xs16 = (unsigned short *)pp.xh;
         u32 *xs32 = (u32 *)pp.xh;
-        if (pp.small && pp.nv == 4) k_x_stage<unsigned short, 4><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
+        if (pp.tiny) k_x_stage<unsigned char, 1><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, (unsigned char *)pp.xh);
+        else if (pp.small && pp.nv == 4) k_x_stage<unsigned short, 4><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
         else if (pp.small && pp.nv == 2) k_x_stage<unsigned short, 2><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
         else if (pp.small) k_x_stage<unsigned short, 1><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs16);
         else if (pp.nv == 2) k_x_stage<u32, 2><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs32);
         else k_x_stage<u32, 1><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs32);
         FF_CUDA(cudaGetLastError());
     }
-    const PanelKernel kf = panel_kernel(pp.small, pp.nv);
+    const PanelKernel kf = panel_kernel(pp.small, pp.nv, pp.tiny);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(pp.ngroup * pp.q), 1, 1);

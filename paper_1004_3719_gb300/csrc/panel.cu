@@ -39,10 +39,13 @@ struct SEnt {
     u32 neg;  // +-1 sections: 1 for a -1 entry
 };
 
-// Bank of x element idx (xb bytes per column: 2, 4, 8 or 16) and of the row
+// Bank of x element idx (xb bytes per column: 1, 2, 4, 8 or 16) and of the row
 // sums of a row (ab bytes per row: 4 to 32); wider words are numbered by
 // their 4-byte bank group, so that distinct numbers mean distinct banks.
-inline int xbank_of(u32 idx, int xb) { return xb == 2 ? (int)((idx >> 1) & 31u) : (int)(idx % (128u / xb)); }
+inline int xbank_of(u32 idx, int xb)
+{
+    return xb == 1 ? (int)((idx >> 2) & 31u) : xb == 2 ? (int)((idx >> 1) & 31u) : (int)(idx % (128u / xb));
+}
 inline int rbank_of(u32 row, int ab) { return (int)(row % (128u / ab)); }
 
 // Single entries keyed by (x bank, row-sum bank).
@@ -260,7 +263,10 @@ void lay_stage(const std::vector<SEnt> &ents, const std::vector<unsigned char> &
     st.npg = (u32)(8 * lpg);
     st.npp = (u32)(8 * lpp);
     ent_out.resize(ent_out.size() + 8 * (size_t)nl);
-    val_out.resize(val_out.size() + 8 * (size_t)nlg);
+    // u8 values (xb == 1) are padded to 16 per stage: the bulk copies of a
+    // stage's values start and end on 16-byte boundaries
+    const size_t vpad = xb == 1 ? 16 : 8;
+    val_out.resize((val_out.size() + 8 * (size_t)nlg + vpad - 1) / vpad * vpad);
     for (int t = 0; t < nl; ++t) {
         const int b0 = t / 32 * 32, j = t - b0, c = std::min(32, nl - b0);
         const int cg = std::min(32, nlg - b0);
@@ -309,9 +315,10 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     for (long long i = 0; i < n; ++i) nnz += len(i);
     if (n <= 0 || nc <= 0 || nnz == 0 || nnz >= (1LL << 31) || nc >= (1LL << 31) - 65536) return false;
     const bool small = m <= 65536u;
+    const bool tiny = m <= 256u && nv == 1;  // u8 x and values (one vector per pass)
     if (nv != 1 && nv != 2 && !(nv == 4 && small)) return false;
     // bytes of x per column and of row sums per row: nv vectors interleaved
-    const int xb = (small ? 2 : 4) * nv, vb = small ? 2 : 4, ab = (small ? 4 : 8) * nv;
+    const int xb = tiny ? 1 : (small ? 2 : 4) * nv, vb = tiny ? 1 : small ? 2 : 4, ab = (small ? 4 : 8) * nv;
     const int ebytes = 4 + vb;
     const int min_sb = 8192 + 1024 * ebytes;
     const long long rcap = std::min<long long>(65536, (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
@@ -370,8 +377,9 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     long long pcols = (long long)((double)sb / ((double)xb + 1.15 * ebytes * dens));
     pcols = std::min<long long>({pcols, (long long)(kPanelIdxMask + 1), (W + cstep - 1) / cstep * cstep});
     pcols = std::max<long long>(cstep, pcols / cstep * cstep);
-    const long long pe = std::min<long long>((sb - pcols * xb) / ebytes / 64 * 64, kPanelMaxPe / 64 * 64);
-    if (pe < 64) return false;
+    const long long pg = tiny ? 128 : 64;  // pe * ebytes a multiple of 128
+    const long long pe = std::min<long long>((sb - pcols * xb) / ebytes / pg * pg, kPanelMaxPe / pg * pg);
+    if (pe < pg) return false;
     const long long eb = pe * ebytes;  // a multiple of 128
     const size_t smem = (size_t)(kPanelStages * (pcols * xb + eb) + kPanelBarBytes + kPanelDescBytes + acc_bytes);
 
@@ -486,11 +494,12 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     // here: 16-byte aligned sources and sizes, stages within the buffers,
     // sections within the stage, panels within the staged x copy
     for (const PanelStage &st : H.stage) {
-        const bool ok = st.k0 % 8 == 0 && st.v0 % 8 == 0 && st.nent % 8 == 0 && st.ngen % 8 == 0 &&
+        const bool ok = st.k0 % 8 == 0 && st.v0 % (tiny ? 16 : 8) == 0 && st.nent % 8 == 0 && st.ngen % 8 == 0 &&
+                        (!tiny || (size_t)st.v0 + (st.ngen + 15) / 16 * 16 <= H.val.size()) &&
                         st.npg % 8 == 0 && st.npp % 8 == 0 && st.nent <= (u32)pe && st.ngen <= st.nent &&
                         st.npg <= st.ngen && st.npp <= st.nent - st.ngen &&
                         (size_t)st.k0 + st.nent <= H.ent.size() && (size_t)st.v0 + st.ngen <= H.val.size() &&
-                        ((size_t)st.xoff * xb) % 128 == 0 && (long long)st.xoff < nc && (st.xs & kPanelSlotMask) < (u32)kPanelStages;
+                        ((size_t)st.xoff * xb) % 16 == 0 && (long long)st.xoff < nc && (st.xs & kPanelSlotMask) < (u32)kPanelStages;
         if (!ok) return false;
     }
     for (u32 w : H.ent)
@@ -501,6 +510,7 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
         H.stage.push_back(st);
     }
     H.small = small;
+    H.tiny = tiny;
     H.nv = nv;
     H.q = q;
     H.ngroup = (int)ng;
@@ -543,7 +553,7 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
     const bool ok = panel_layout(nrows, ncols, (const long long *)row_ptr, c.data(), v.data(), cls.data(), m,
                                  use_pm1 == 1, q, nv, [&](int cq, bool) { return cq == q ? clusters : 0; }, H);
     if (!ok) return FFSPMV_ERR_UNSUPPORTED;
-    const int xb = (H.small ? 2 : 4) * nv, ab = (H.small ? 4 : 8) * nv;  // bytes per column / per row
+    const int xb = H.tiny ? 1 : (H.small ? 2 : 4) * nv, ab = (H.small ? 4 : 8) * nv;  // bytes per column / per row
     long long n = 0, lanes = 0, packs = 0, bad_packs = 0;
     double gwf = 0, awf = 0, slots = 0, aslots = 0;
     for (long long cta = 0; cta < (long long)H.ngroup * H.q; ++cta) {
@@ -572,7 +582,7 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
                             value = (w[u] & kPanelNeg) ? m - 1u : 1u;
                         }
                         const u32 idx = w[u] & kPanelIdxMask;
-                        xw[u][nxw[u]++] = (int)(xb == 2 ? idx >> 1 : idx * (u32)(xb / 4));  // first 4-byte word
+                        xw[u][nxw[u]++] = (int)(xb == 1 ? idx >> 2 : xb == 2 ? idx >> 1 : idx * (u32)(xb / 4));  // first 4-byte word
                         if (!pack) rw[u][nrw[u]++] = (int)(w[u] >> 16);
                         if (value == 0) continue;  // padding
                         if (n < cap) {

@@ -648,18 +648,23 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, int nv, 
     const bool pm_on = use_pm1 == 1 || (use_pm1 < 0 && nnz > 0 && npm * 20 >= nnz);
     PanelHost H;
     if (!panel_layout(A.nrows, A.ncols, A.ptr.data(), A.col.data(), A.val.data(), A.cls.data(), m, pm_on,
-                      force_q, nv, [nv](int q, bool small) { return panel_max_clusters(small, nv, q, kPanelSmemMax); },
+                      force_q, nv,
+                      [nv, m](int q, bool small) {
+                          return panel_max_clusters(small, nv, q, kPanelSmemMax, m <= 256u && nv == 1);
+                      },
                       H))
         return false;
-    const int vb = H.small ? 2 : 4, xb = H.small ? 2 : 4;
+    const int vb = H.tiny ? 1 : H.small ? 2 : 4, xb = vb;
     std::vector<unsigned char> vbytes(H.val.size() * vb + 64, 0);
     for (size_t t = 0; t < H.val.size(); ++t) {
-        if (vb == 2) ((unsigned short *)vbytes.data())[t] = (unsigned short)H.val[t];
+        if (vb == 1) vbytes[t] = (unsigned char)H.val[t];
+        else if (vb == 2) ((unsigned short *)vbytes.data())[t] = (unsigned short)H.val[t];
         else ((u32 *)vbytes.data())[t] = H.val[t];
     }
     H.ent.resize(H.ent.size() + 16, 0);
     pp.on = true;
     pp.small = H.small;
+    pp.tiny = H.tiny;
     pp.nv = H.nv;
     pp.q = H.q;
     pp.ngroup = H.ngroup;
@@ -928,7 +933,7 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                  " + %d entries, x staged as %s, %s row sums, %d vector(s) per pass, %lld entries in +-1 sections,"
                  " %lld padding\n",
                  P.panel.ngroup, P.panel.q, P.panel.q, P.panel.resident, P.panel.nstage, P.panel.px, P.panel.pe,
-                 P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64", P.panel.nv, P.panel.npm,
+                 P.panel.tiny ? "u8" : P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64", P.panel.nv, P.panel.npm,
                  P.panel.npad);
         P.summary += buf;
         return FFSPMV_OK;

@@ -185,6 +185,29 @@ def test_panel_one_vector_passes_stage_groups(lib, m):
     check_apply(lib, MB, B, nvec=6, seed=77)
 
 
+@pytest.mark.parametrize("m", [2, 3, 251, 256])
+def test_panel_u8_moduli(lib, m):
+    """m <= 256: the x-panel layout stages x and stores values as u8 and adds
+    the products v x < 2^16 unreduced; products, transposes, blocks (one
+    staging launch per four vectors) and the longest panel rows at the worst
+    values, against the oracle."""
+    A = gen.powerlaw_matrix(seed=23, n=40_009, lmax=3000, m=m, pm_fraction=0.3)
+    for pm in (0, 1):
+        M = make(lib, A, "PANEL", use_pm1=pm)
+        assert "x staged as u8" in M.describe()
+        check_apply(lib, M, A, alpha=1 % m, beta=(m - 1) % m, seed=3 + pm)
+        check_apply(lib, M, A, transpose=True, seed=5 + pm)
+        check_apply(lib, M, A, nvec=5, seed=7 + pm)
+    lengths = np.array([32_768, 32_769, 17, 0, 1])
+    nc = 70_000
+    col = np.concatenate([np.arange(L) * 2 for L in lengths]).astype(np.int32)
+    W = gen.CSR(lengths.size, nc, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col,
+                np.full(lengths.sum(), m - 1, dtype=np.uint32), m)
+    MW = make(lib, W, "PANEL", use_pm1=0, transpose_mode=lib.TRANSPOSE.NONE)
+    y = to_host(MW.apply(to_dev(np.full(nc, m - 1, dtype=np.uint32))))
+    assert list(y) == [int(L) * (m - 1) * (m - 1) % m for L in lengths]
+
+
 def test_panel_wide_passes_kept_only_when_faster(lib):
     """Without the test hook a block on the 1M power-law matrix (few entries
     per column of a CTA) keeps one-vector passes if the timed 2-vector pass
