@@ -440,40 +440,41 @@ def write_report(args, result, rows):
         "(one GB300).",
         "",
         f"* corpus: {result['train_matrices']} training + {result['test_matrices']} held-out matrices, "
-        f"{result['train_samples']} (matrix, bin) training samples; corpus {result['corpus_seconds']} s, "
-        f"training {result['train_seconds']} s",
+        f"{result['train_samples']} training samples ((matrix, bin) pairs and matrix-level rows); corpus "
+        f"{result['corpus_seconds']} s, training {result['train_seconds']} s",
         f"* loss (masked squared error of log time ratios): {result['losses'][0][1]:.4f} at step 1, "
         f"{result['losses'][-1][1]:.4f} at step {result['losses'][-1][0]}",
-        "",
-        "Held-out share of exhaustive-best throughput (cost model: per-bin sample times x bin entries):",
-        "",
-        "| chooser | mean | median | min |",
-        "|---|---|---|---|",
     ]
-    for k in ("learned", "heuristic", "fixed_csr"):
-        lines.append(f"| {k} | {100 * s[k]['mean']:.1f}% | {100 * s[k]['median']:.1f}% | {100 * s[k]['min']:.1f}% |")
     w = result["whole_plan"]
     if w:
-        lines += ["", "Held-out whole-plan layout choice: best of (binned with the heuristic table, binned with "
-                  "the exhaustive table, x-panel) over the time of the layout each chooser picks "
-                  "(learned: the network's matrix-level outputs; heuristic: the AUTO panel rule; exhaustive: the "
-                  "faster of its binned plan and the x-panel plan):", "",
-                  "| chooser | mean | median | min |", "|---|---|---|---|"]
+        t = result["total_us"]
+        lines += ["", "## Whole-matrix time of y = A x (the headline)", "",
+                  f"Summed over the held-out matrices: **{t['learned']:.0f} µs with the learned selector vs "
+                  f"{t['heuristic']:.0f} µs with the heuristic AUTO rule**. Per matrix, the best whole-plan time "
+                  "(binned with the heuristic table, binned with the exhaustive table, x-panel with 1, 2 or 4 CTAs "
+                  "per cluster) over the time of the layout each chooser gets (learned: the library's rule on the "
+                  "network's matrix-level outputs, with its timed check of close calls; heuristic: the AUTO panel "
+                  "rule; exhaustive: the faster of its binned plan and the x-panel plan), L2 flushed, median of 7:",
+                  "", "| chooser | mean | median | min |", "|---|---|---|---|"]
         for k in ("learned", "heuristic", "exhaustive"):
             lines.append(f"| {k} | {100 * w[k]['mean']:.1f}% | {100 * w[k]['median']:.1f}% | "
                          f"{100 * w[k]['min']:.1f}% |")
-        t = result["total_us"]
-        lines += ["", f"Layouts the network picked: {result['layouts']}, {t['verified']} of them checked by timing "
-                  f"both families; summed held-out time {t['learned']:.0f} µs (learned) vs {t['heuristic']:.0f} µs "
-                  "(heuristic AUTO)."]
+        lines += ["", f"Layouts the network picked: {result['layouts']}; {t['verified']} close calls checked by "
+                  "timing both families."]
     if result["e2e"]:
-        lines += ["", "Whole-matrix y = A x of the FMT.AUTO handles per selector (µs, median of 10, L2 flushed; "
-                  "layout in brackets):", "",
+        lines += ["", "FMT.AUTO handles built by the library under each selector, timed whole (µs, median of 10, "
+                  "L2 flushed; layout in brackets):", "",
                   "| matrix | nnz | learned | exhaustive | heuristic | fixed CSR |", "|---|---|---|---|---|---|"]
         for e in result["e2e"]:
             lines.append(f"| {e['name']} | {e['nnz']} | {e['learned_us']} ({e['learned_layout']}) | "
                          f"{e['exhaustive_us']} ({e['exhaustive_layout']}) | "
                          f"{e['heuristic_us']} ({e['heuristic_layout']}) | {e['fixed_csr_us']} |")
+    lines += ["", "## Per-bin format choice (cost model of the exhaustive search's sample timings)", "",
+              "Held-out share of exhaustive-best throughput, the cost of a choice being the sum over bins of "
+              "(sample time per entry) x (entries of the bin):", "",
+              "| chooser | mean | median | min |", "|---|---|---|---|"]
+    for k in ("learned", "heuristic", "fixed_csr"):
+        lines.append(f"| {k} | {100 * s[k]['mean']:.1f}% | {100 * s[k]['median']:.1f}% | {100 * s[k]['min']:.1f}% |")
     with open(args.report, "w") as f:
         f.write("\n".join(lines) + "\n")
 
