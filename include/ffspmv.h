@@ -63,7 +63,8 @@ enum {
     FFSPMV_FMT_HYBRID = 6,  /* paper heuristic: DIA + ELL_R(w) + CSR/COO/COO_S residue (Sec. 2.4.5) */
     FFSPMV_FMT_BINNED = 7,  /* rows binned by length, one format per bin */
     FFSPMV_FMT_PANEL = 8    /* row groups x column groups (CTA clusters), x streamed through
-                               shared memory in panels (not in the paper) */
+                               shared memory in panels (not in the paper); x staged as u8
+                               (m <= 256), u16 (m <= 2^16) or u32 */
 };
 
 /* Format selectors (how FFSPMV_FMT_AUTO / FFSPMV_FMT_BINNED pick). */
