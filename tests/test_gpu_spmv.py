@@ -208,6 +208,25 @@ def test_panel_u8_moduli(lib, m):
     assert list(y) == [int(L) * (m - 1) * (m - 1) % m for L in lengths]
 
 
+@pytest.mark.parametrize("m,q", [(2**31 - 1, 1), (2**31 - 1, 2), (4294967291, 2), (65537, 4)])
+def test_panel_u32_sums_wrap_exactly(lib, m, q):
+    """m > 2^16: the one-vector row sums are u32 that wrap many times (every
+    value and every x at m - 1) and each wrap adds back 2^32 mod m, in the
+    CTA's own sums and in the cluster's cross-CTA adds; the results equal the
+    closed form L (m-1)^2 mod m."""
+    lengths = np.array([32_768, 20_000, 4097, 17, 1, 0, 3000])
+    nc = 120_000
+    rng = np.random.default_rng(q)
+    col = np.concatenate([np.sort(rng.choice(nc, L, replace=False)) for L in lengths]).astype(np.int32)
+    A = gen.CSR(lengths.size, nc, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col,
+                np.full(lengths.sum(), m - 1, dtype=np.uint32), m)
+    M = make(lib, A, "PANEL", panel_cluster=q, use_pm1=0, transpose_mode=lib.TRANSPOSE.NONE)
+    assert "panels:" in M.describe()
+    y = to_host(M.apply(to_dev(np.full(nc, m - 1, dtype=np.uint32))))
+    assert list(y) == [int(L) * (m - 1) * (m - 1) % m for L in lengths]
+    check_apply(lib, M, A, alpha=m - 2, beta=m - 3, seed=q)
+
+
 def test_panel_wide_passes_kept_only_when_faster(lib):
     """Without the test hook a block on the 1M power-law matrix (few entries
     per column of a CTA) keeps one-vector passes if the timed 2-vector pass
