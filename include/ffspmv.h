@@ -180,6 +180,22 @@ ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X,
                                   ffspmv_stream_t stream);
 
 /*
+ * One step's projection for a sequence whose rows are split over several
+ * processes (each holding rows r0..r1 of A, X and V): d_Sacc[a*s + b] +=
+ * sum over the n rows k of X[k][a] * V[k][b], reduced mod p before it is
+ * added (d_Sacc: s x s uint64, device, zero before the first call; one call
+ * adds at most one value below p per SM to each entry, so the accumulators
+ * of many calls and processes stay far below 2^64).  d_X, d_V: n x s row-major (ld = s), residues below p;
+ * 1 <= s <= 32, p >= 2.  spmv_block_project_finish then writes S = Sacc mod p
+ * (s x s uint32) and zeroes Sacc.  Asynchronous on `stream`; FFSPMV_ERR_ARG
+ * on a bad size or a missing pointer.
+ */
+ffspmv_status spmv_block_project(uint32_t p, int64_t n, int32_t s, const uint32_t *d_X,
+                                 const uint32_t *d_V, uint64_t *d_Sacc, ffspmv_stream_t stream);
+ffspmv_status spmv_block_project_finish(uint32_t p, int32_t s, uint64_t *d_Sacc, uint32_t *d_S,
+                                        ffspmv_stream_t stream);
+
+/*
  * Independent products Y_j = A_j * X_j (mod m_j), j < count, in one launch
  * (not in the paper).  hs: host array of handles (each with its own
  * modulus); d_x / d_y: host arrays of device pointers, X_j: ncols_j x nvec[j]

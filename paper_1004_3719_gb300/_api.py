@@ -85,6 +85,16 @@ def spmv_block_sequence(h, X, Y, s, start_step, nsteps, S, V_state=None, stream=
           "spmv_block_sequence")
 
 
+def spmv_block_project(p, n, s, X, V, Sacc, stream=None):
+    check(lib().spmv_block_project(int(p), int(n), int(s), _ptr(X), _ptr(V), _ptr(Sacc), stream_ptr(stream)),
+          "spmv_block_project")
+
+
+def spmv_block_project_finish(p, s, Sacc, S, stream=None):
+    check(lib().spmv_block_project_finish(int(p), int(s), _ptr(Sacc), _ptr(S), stream_ptr(stream)),
+          "spmv_block_project_finish")
+
+
 def spmv_batch_apply(handles, xs, ys, nvec, stream=None):
     n = len(handles)
     H = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
@@ -294,7 +304,8 @@ def to_numpy_u32(t):
 
 __all__ = ["Matrix", "spmv_create_hybrid", "spmv_apply", "spmv_apply_transpose",
            "spmv_apply_transpose_noalloc",
-           "spmv_block_sequence", "spmv_batch_apply", "spmv_destroy",
+           "spmv_block_sequence", "spmv_block_project", "spmv_block_project_finish",
+           "spmv_batch_apply", "spmv_destroy",
            "spmv_describe_plan", "spmv_get_info", "spmv_count_launches", "spmv_check_status",
            "spmv_apply_gf2", "polymat_mul", "sigma_basis", "sigma_wiedemann_input", "stream_ptr",
            "to_numpy_u32",

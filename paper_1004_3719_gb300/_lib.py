@@ -96,6 +96,10 @@ def _declare(L):
     L.sigma_basis.restype = ctypes.c_int
     L.sigma_wiedemann_input.argtypes = [_U32, _I32, _I64, _P, _P, _P]
     L.sigma_wiedemann_input.restype = ctypes.c_int
+    L.spmv_block_project.argtypes = [_U32, _I64, _I32, _P, _P, _P, _P]
+    L.spmv_block_project.restype = ctypes.c_int
+    L.spmv_block_project_finish.argtypes = [_U32, _I32, _P, _P, _P]
+    L.spmv_block_project_finish.restype = ctypes.c_int
     for name, args, res in EXTRA_SIGNATURES:
         if hasattr(L, name):
             fn = getattr(L, name)

@@ -840,3 +840,37 @@ extern "C" ffspmv_status spmv_block_sequence(ffspmv_t h, const uint32_t *d_X, co
     }
     return FFSPMV_OK;
 }
+
+// The projection of one step on its own, for a sequence whose rows are split
+// over several processes: each adds its rows' X^T V into a u64 accumulator,
+// the accumulators are summed across processes, and the finish reduces them.
+extern "C" ffspmv_status spmv_block_project(uint32_t p, int64_t n, int32_t s, const uint32_t *d_X,
+                                            const uint32_t *d_V, uint64_t *d_Sacc, ffspmv_stream_t stream)
+{
+    if (p < 2 || n < 0 || s < 1 || s > 32 || !d_Sacc || (n > 0 && (!d_X || !d_V))) return FFSPMV_ERR_ARG;
+    if (n == 0) return FFSPMV_OK;
+    const Mod M = make_mod(p, 1, 0);
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned pg = (unsigned)std::max<long long>(1, std::min<long long>(n, (long long)std::max(nsm, 1)));
+    const bool wide = (unsigned long long)(p - 1) * (p - 1) > (~0ull) / (unsigned long long)n;
+    if (wide)
+        k_project<AccWide><<<pg, 256, 0, st>>>(n, s, d_X, d_V, (u64 *)d_Sacc, M);
+    else
+        k_project<AccSmall><<<pg, 256, 0, st>>>(n, s, d_X, d_V, (u64 *)d_Sacc, M);
+    FF_CUDA(cudaGetLastError());
+    return FFSPMV_OK;
+}
+
+extern "C" ffspmv_status spmv_block_project_finish(uint32_t p, int32_t s, uint64_t *d_Sacc, uint32_t *d_S,
+                                                   ffspmv_stream_t stream)
+{
+    if (p < 2 || s < 1 || s > 32 || !d_Sacc || !d_S) return FFSPMV_ERR_ARG;
+    const Mod M = make_mod(p, 1, 0);
+    const int outs = s * s;
+    k_project_finish<<<(outs + 255) / 256, 256, 0, (cudaStream_t)stream>>>(outs, (u64 *)d_Sacc, d_S, M);
+    FF_CUDA(cudaGetLastError());
+    return FFSPMV_OK;
+}
