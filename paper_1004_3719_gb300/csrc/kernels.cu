@@ -868,27 +868,33 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
             const u32 vbytes = TINY ? (a.ngen + 15u) & ~15u : a.ngen * (u32)VB;
             const u32 dbytes = a.nent * 4u + vbytes;
             if (lane == 1) mbar_add_tx(bar, dbytes);
-            __syncwarp();  // the bytes are added before lane 0's arrive
-            if (lane == 1) {
-                bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
-                if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, vbytes, bar);
+            __syncwarp();  // the entry bytes are added before lane 0's arrive
+            if (lane == 1) bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
+            if (lane == 2 && a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, vbytes, bar);
+            // the x panel in kPanelXSplit pieces from lanes 0 and 3.. (a thread's
+            // bulk copies complete one after another)
+            const bool newx = (a.xs & kPanelNewX) != 0;
+            const bool xlane = lane == 0 || (lane >= 3 && lane < 2 + kPanelXSplit);
+            if (xlane && !xready) {
+                // every CTA's share of x is staged before the first panel copy
+                unsigned spin = 0;
+                while (ld_acquire_gpu(P.gbar + 1) == s_gen)
+                    if (++spin >= kPanelGridSpin) {
+                        timed_out = true;
+                        break;
+                    }
+                fence_proxy_async_global();
+                xready = true;
             }
             if (lane == 0) {
-                if (!xready) {
-                    // every CTA's share of x is staged before the first panel copy
-                    unsigned spin = 0;
-                    while (ld_acquire_gpu(P.gbar + 1) == s_gen)
-                        if (++spin >= kPanelGridSpin) {
-                            timed_out = true;
-                            break;
-                        }
-                    fence_proxy_async_global();
-                    xready = true;
-                }
-                const bool newx = (a.xs & kPanelNewX) != 0;
                 desc[b] = make_uint4(a.nent, a.ngen, a.npg | (a.npp << 16), a.xs & kPanelSlotMask);  // published by the arrive
                 mbar_expect_tx(bar, newx ? (u32)PX : 0u);
-                if (newx) bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX, xh + (size_t)a.xoff * sizeof(XW), (u32)PX, bar);
+            }
+            __syncwarp();  // the arrive with the panel's bytes comes before its copies
+            if (xlane && newx) {
+                const u32 part = lane == 0 ? 0u : (u32)lane - 2u, piece = (u32)PX / kPanelXSplit;
+                bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX + part * piece,
+                         xh + (size_t)a.xoff * sizeof(XW) + part * piece, piece, bar);
             }
             __syncwarp();
         }
