@@ -213,7 +213,6 @@ constexpr u32 kPanelNewX = 8u;                // PanelStage::xs: the panel is co
 static_assert(16 * kPanelStages + 8 <= kPanelBarBytes && kPanelStages <= 7,
               "full and empty mbarriers of the stage buffers, the epilogue's receive mbarrier, x slots");
 constexpr unsigned kPanelSpin = 1u << 20;     // polls of an mbarrier before giving up
-constexpr unsigned kPanelXSplit = 4;          // bulk copies (lanes) per x panel (px is a multiple of 128)
 constexpr unsigned kPanelGridSpin = 1u << 20; // polls of the grid barrier before giving up
 constexpr u32 kPanelIdxMask = 0x7fffu;        // x element of the panel
 constexpr u32 kPanelNeg = 0x8000u;            // a -1 entry (+-1 sections)

@@ -556,19 +556,6 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// *p += t where *p keeps a sum mod 2^32: when the add wraps, the 2^32 it lost
-// is added back as c32 = 2^32 mod m (which may wrap again, and so on), so *p
-// stays congruent to the exact sum mod m.  A wrap of a compensating add needs
-// the sum within c32 of 2^32, so the loop ends after a few rounds.
-__device__ __forceinline__ void add_wrap(u32 *p, u32 t, u32 c32)
-{
-    for (int i = 0; i < 1024; ++i) {
-        const u32 old = atomicAdd(p, t);
-        if (old + t >= old || c32 == 0u) return;
-        t = c32;
-    }
-}
-
 // The shared::cluster address of `local` in CTA `rank` of the cluster.
 template <typename T>
 __device__ __forceinline__ u32 map_cluster(const T *local, u32 rank)
@@ -576,17 +563,6 @@ __device__ __forceinline__ u32 map_cluster(const T *local, u32 rank)
     u32 r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((u32)__cvta_generic_to_shared(local)), "r"(rank));
     return r;
-}
-
-// add_wrap on another CTA's shared memory.
-__device__ __forceinline__ void add_wrap_cluster(u32 addr, u32 t, u32 c32)
-{
-    for (int i = 0; i < 1024; ++i) {
-        u32 old;
-        asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(t) : "memory");
-        if (old + t >= old || c32 == 0u) return;
-        t = c32;
-    }
 }
 
 // *addr += v in another CTA's shared memory (posted; ordered by the next cluster barrier).
@@ -707,11 +683,7 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     static_assert(!TINY || (SMALL && NV == 1), "u8 x: one vector, m <= 256");
     typedef typename std::conditional<TINY, unsigned char,
                                       typename std::conditional<SMALL, unsigned short, u32>::type>::type XT;
-    // row sums: u32, except u64 for 2- and 4-vector passes at m > 2^16; at
-    // m > 2^16 with one vector the u32 sums wrap, and every wrap adds back
-    // 2^32 mod m (add_wrap), so they stay congruent to the exact sums
-    typedef typename std::conditional<SMALL || NV == 1, u32, u64>::type AT;
-    const u32 c32 = SMALL ? 0u : red64((u64)1 << 32, M);  // 2^32 mod m
+    typedef typename std::conditional<SMALL, u32, u64>::type AT;
     // a lane's term: one row sum's (AT), or, for 16-bit residues and NV > 1,
     // two vectors' u32 sums side by side in a u64 (each half stays below
     // 2^32, the bound of a single row sum, so no carry crosses between them)
@@ -868,33 +840,27 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
             const u32 vbytes = TINY ? (a.ngen + 15u) & ~15u : a.ngen * (u32)VB;
             const u32 dbytes = a.nent * 4u + vbytes;
             if (lane == 1) mbar_add_tx(bar, dbytes);
-            __syncwarp();  // the entry bytes are added before lane 0's arrive
-            if (lane == 1) bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
-            if (lane == 2 && a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, vbytes, bar);
-            // the x panel in kPanelXSplit pieces from lanes 0 and 3.. (a thread's
-            // bulk copies complete one after another)
-            const bool newx = (a.xs & kPanelNewX) != 0;
-            const bool xlane = lane == 0 || (lane >= 3 && lane < 2 + kPanelXSplit);
-            if (xlane && !xready) {
-                // every CTA's share of x is staged before the first panel copy
-                unsigned spin = 0;
-                while (ld_acquire_gpu(P.gbar + 1) == s_gen)
-                    if (++spin >= kPanelGridSpin) {
-                        timed_out = true;
-                        break;
-                    }
-                fence_proxy_async_global();
-                xready = true;
+            __syncwarp();  // the bytes are added before lane 0's arrive
+            if (lane == 1) {
+                bulk_g2s(d, ev + (size_t)a.k0 * 4, a.nent * 4u, bar);
+                if (a.ngen) bulk_g2s(d + 4u * P.pe, vv + (size_t)a.v0 * VB, vbytes, bar);
             }
             if (lane == 0) {
+                if (!xready) {
+                    // every CTA's share of x is staged before the first panel copy
+                    unsigned spin = 0;
+                    while (ld_acquire_gpu(P.gbar + 1) == s_gen)
+                        if (++spin >= kPanelGridSpin) {
+                            timed_out = true;
+                            break;
+                        }
+                    fence_proxy_async_global();
+                    xready = true;
+                }
+                const bool newx = (a.xs & kPanelNewX) != 0;
                 desc[b] = make_uint4(a.nent, a.ngen, a.npg | (a.npp << 16), a.xs & kPanelSlotMask);  // published by the arrive
                 mbar_expect_tx(bar, newx ? (u32)PX : 0u);
-            }
-            __syncwarp();  // the arrive with the panel's bytes comes before its copies
-            if (xlane && newx) {
-                const u32 part = lane == 0 ? 0u : (u32)lane - 2u, piece = (u32)PX / kPanelXSplit;
-                bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX + part * piece,
-                         xh + (size_t)a.xoff * sizeof(XW) + part * piece, piece, bar);
+                if (newx) bulk_g2s(sbase + (a.xs & kPanelSlotMask) * PX, xh + (size_t)a.xoff * sizeof(XW), (u32)PX, bar);
             }
             __syncwarp();
         }
@@ -923,11 +889,8 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                     // one vector: terms and sums per lane value as u32 (m <= 2^16) or u64
                         const u32 tl = lb + lane, c = min(32u, nl - lb);
                         const bool valid = tl < nl, general = tl < nlg;
-                        // terms and pack sums: u32 (m <= 2^16), else u64 (eight terms
-                        // below m can pass 2^32), reduced below m before an atomic
-                        typedef typename std::conditional<SMALL, u32, u64>::type ST;
                         u32 e[8];
-                        ST tm[8];
+                        AT tm[8];
     #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             e[u] = 0;
@@ -962,15 +925,15 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     #pragma unroll
                                 for (int u = 0; u < 8; ++u) {
                                     const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
-                                    tm[u] = TINY ? (ST)(v[u] * xv)
-                                                 : SMALL ? (ST)red32_lazy(v[u] * xv, M.m, mu32) : (ST)red64((u64)v[u] * xv, M);
+                                    tm[u] = TINY ? (AT)(v[u] * xv)
+                                                 : SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
                                 }
                             } else {
                                 // +-1 sections (Sec. 2.4.2): x or m - x, no value
     #pragma unroll
                                 for (int u = 0; u < 8; ++u) {
                                     const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
-                                    tm[u] = (ST)((e[u] & kPanelNeg) ? M.m - xv : xv);
+                                    tm[u] = (AT)((e[u] & kPanelNeg) ? M.m - xv : xv);
                                 }
                             }
                         }
@@ -989,27 +952,21 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                             // Packs of one row are adjacent within each section; a row
                             // can have packs in both sections, so the +-1 packs get keys
                             // of their own (the runs the sum joins must be contiguous)
-                            ST sum = 0;
+                            AT sum = 0;
                             if (pack) sum = ((tm[0] + tm[1]) + (tm[2] + tm[3])) + ((tm[4] + tm[5]) + (tm[6] + tm[7]));
                             const u32 key = pack ? ((e[0] >> 16) | (general ? 0u : 0x20000u)) : (0x10000u + (u32)lane);
     #pragma unroll
                             for (int d = 1; d < 32; d <<= 1) {
-                                const ST o = __shfl_down_sync(0xffffffffu, sum, d);
+                                const AT o = __shfl_down_sync(0xffffffffu, sum, d);
                                 const u32 k2 = __shfl_down_sync(0xffffffffu, key, d);
                                 if (lane + d < 32 && k2 == key) sum += o;
                             }
                             const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
-                            if (pack && (lane == 0 || kp != key)) {
-                                if constexpr (SMALL) atomicAdd(acc + (key & 0xffffu), sum);
-                                else add_wrap(acc + (key & 0xffffu), red64(sum, M), c32);
-                            }
+                            if (pack && (lane == 0 || kp != key)) atomicAdd(acc + (key & 0xffffu), sum);
                         }
                         if (valid && !pack) {
     #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                if constexpr (SMALL) atomicAdd(acc + (e[u] >> 16), tm[u]);
-                                else add_wrap(acc + (e[u] >> 16), (u32)tm[u], c32);
-                            }
+                            for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> 16), tm[u]);
                         }
                     } else {
                         const u32 tl = lb + lane, c = min(32u, nl - lb);
@@ -1147,10 +1104,7 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
             const u32 base = map_cluster(acc, (u32)j);
             for (u32 f = jb + t; f < je; f += kPanelThreads) {
                 const AT v = acc[f];
-                if (v) {
-                    if constexpr (!SMALL && NV == 1) add_wrap_cluster(base + f * 4u, v, c32);
-                    else red_cluster_add(base + f * (u32)sizeof(AT), v);
-                }
+                if (v) red_cluster_add(base + f * (u32)sizeof(AT), v);
             }
         }
         cluster_sync_all();  // every partial sum of this CTA's share has arrived

@@ -318,9 +318,7 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     const bool tiny = m <= 256u && nv == 1;  // u8 x and values (one vector per pass)
     if (nv != 1 && nv != 2 && !(nv == 4 && small)) return false;
     // bytes of x per column and of row sums per row: nv vectors interleaved
-    // row sums: u32 (m <= 2^16: bounded; m > 2^16, one vector: kept mod 2^32 with each wrap added back as
-    // 2^32 mod m), u64 for wider passes at m > 2^16
-    const int xb = tiny ? 1 : (small ? 2 : 4) * nv, vb = tiny ? 1 : small ? 2 : 4, ab = (small || nv == 1 ? 4 : 8) * nv;
+    const int xb = tiny ? 1 : (small ? 2 : 4) * nv, vb = tiny ? 1 : small ? 2 : 4, ab = (small ? 4 : 8) * nv;
     const int ebytes = 4 + vb;
     const int min_sb = 8192 + 1024 * ebytes;
     const long long rcap = std::min<long long>(65536, (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
@@ -555,7 +553,7 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
     const bool ok = panel_layout(nrows, ncols, (const long long *)row_ptr, c.data(), v.data(), cls.data(), m,
                                  use_pm1 == 1, q, nv, [&](int cq, bool) { return cq == q ? clusters : 0; }, H);
     if (!ok) return FFSPMV_ERR_UNSUPPORTED;
-    const int xb = H.tiny ? 1 : (H.small ? 2 : 4) * nv, ab = (H.small || nv == 1 ? 4 : 8) * nv;  // bytes per column / per row
+    const int xb = H.tiny ? 1 : (H.small ? 2 : 4) * nv, ab = (H.small ? 4 : 8) * nv;  // bytes per column / per row
     long long n = 0, lanes = 0, packs = 0, bad_packs = 0;
     double gwf = 0, awf = 0, slots = 0, aslots = 0;
     for (long long cta = 0; cta < (long long)H.ngroup * H.q; ++cta) {
