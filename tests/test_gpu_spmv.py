@@ -209,11 +209,10 @@ def test_panel_u8_moduli(lib, m):
 
 
 @pytest.mark.parametrize("m,q", [(2**31 - 1, 1), (2**31 - 1, 2), (4294967291, 2), (65537, 4)])
-def test_panel_u32_sums_wrap_exactly(lib, m, q):
-    """m > 2^16: the one-vector row sums are u32 that wrap many times (every
-    value and every x at m - 1) and each wrap adds back 2^32 mod m, in the
-    CTA's own sums and in the cluster's cross-CTA adds; the results equal the
-    closed form L (m-1)^2 mod m."""
+def test_panel_wide_sums_at_worst_values(lib, m, q):
+    """m > 2^16: every value and every x at m - 1, long rows split over the
+    column groups of a cluster (the CTAs' u64 partial sums meet in the
+    cluster epilogue); the results equal the closed form L (m-1)^2 mod m."""
     lengths = np.array([32_768, 20_000, 4097, 17, 1, 0, 3000])
     nc = 120_000
     rng = np.random.default_rng(q)
