@@ -294,7 +294,9 @@ ffspmv_status spmv_check_status(ffspmv_t h, ffspmv_stream_t stream);
  * Testing aid for the x-panel layout (FFSPMV_FMT_PANEL); the paper has no
  * counterpart.  Runs only the host half of the layout for the CSR matrix
  * (row_ptr, col, values as in spmv_create_hybrid, host memory) with q CTAs
- * per cluster (1, 2 or 4), `clusters` resident clusters and nv vectors per
+ * per cluster (1, 2 or 4; 0 = the builder's choice, with clusters / q
+ * resident clusters of q, stats[9] telling which), `clusters` resident
+ * clusters and nv vectors per
  * pass (1, 2, or 4 when m <= 2^16: the geometry of the layout that a block
  * of that many vectors runs on), then decodes
  * every stored entry back to (row, column, value) and writes the first `cap`

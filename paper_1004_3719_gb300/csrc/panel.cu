@@ -324,9 +324,33 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     const long long rcap = std::min<long long>(65536, (kPanelSmemMax - kPanelBarBytes - kPanelDescBytes -
                                                        kPanelStages * min_sb) / ab);
 
+    // column counts, and column groups of q balanced by entries with
+    // boundaries on multiples of 64 columns
+    std::vector<long long> ccount((size_t)nc, 0);
+    for (long long i = 0; i < n; ++i)
+        if (len(i))
+            for (long long k = ptr[i]; k < ptr[i + 1]; ++k) ccount[col[k]]++;
+    auto col_bounds = [&](int cq) {
+        std::vector<long long> b{0};
+        long long cur = 0;
+        for (long long c = 0; c < nc && (int)b.size() < cq; ++c) {
+            cur += ccount[c];
+            if (cur * cq >= nnz * (long long)b.size() && (c + 1) % 64 == 0 && c + 1 < nc) b.push_back(c + 1);
+        }
+        while ((int)b.size() < cq) b.push_back(nc);  // empty trailing groups
+        b.push_back(nc);
+        return b;
+    };
+
     // cluster size (column groups): the fewest waves of clusters, then the
     // most SMs busy, then the larger q; row groups, one per resident
     // cluster, balanced by entries under the shared-memory row cap
+    struct Cand {
+        int c = 0;
+        long long waves = 0, used = 0;
+        std::vector<u32> r;
+    };
+    Cand cand[3];
     int q = 0, nclus = 0;
     long long best_waves = 0, best_used = 0;
     std::vector<u32> row0;
@@ -338,6 +362,11 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
         std::vector<u32> r = row_groups(n, len, nnz, c, rcap);
         const long long G = (long long)r.size() - 1;
         const long long waves = (G + c - 1) / c, used = std::min<long long>(G, c) * cq;
+        Cand &k = cand[cq == 1 ? 0 : cq == 2 ? 1 : 2];
+        k.c = c;
+        k.waves = waves;
+        k.used = used;
+        k.r = r;
         if (q == 0 || waves < best_waves || (waves == best_waves && used >= best_used)) {
             q = cq;
             nclus = c;
@@ -347,25 +376,36 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
         }
     }
     if (q == 0) return false;
+    if (force_q <= 0 && cand[0].c > 0 && cand[1].c > 0 && cand[0].waves == 1 && cand[1].waves == 1) {
+        // One or two CTAs per cluster, both in one wave: two only when the
+        // columns are spread over the row groups (each row group's entries
+        // split about evenly between the two column groups: local structure
+        // such as bands or blocks leaves one CTA of each pair idle) and x
+        // outweighs the entries in what a CTA streams (x bytes of all
+        // columns at least twice a CTA's entry bytes).  Rule read off
+        // whole-plan timings of 1 350 generated matrices; clusters of four
+        // rarely won there.
+        const std::vector<long long> b2 = col_bounds(2);
+        const std::vector<u32> &r2 = cand[1].r;
+        long long sum_max = 0;
+        for (size_t g = 0; g + 1 < r2.size(); ++g) {
+            long long e0 = 0, e1 = 0;
+            for (long long i = r2[g]; i < (long long)r2[g + 1]; ++i)
+                if (len(i))
+                    for (long long k = ptr[i]; k < ptr[i + 1]; ++k) (col[k] < (u32)b2[1] ? e0 : e1)++;
+            sum_max += std::max(e0, e1);
+        }
+        const bool balanced = 2.0 * (double)sum_max <= 1.25 * (double)nnz;
+        const double x_over_e = (double)nc * xb * cand[0].c / ((double)nnz * ebytes);
+        const int pick = balanced && x_over_e >= 2.0 ? 1 : 0;
+        q = pick ? 2 : 1;
+        nclus = cand[pick].c;
+        row0 = cand[pick].r;
+    }
     const long long ng = (long long)row0.size() - 1;
     long long rows_max = 1;
     for (long long g = 0; g < ng; ++g) rows_max = std::max<long long>(rows_max, row0[g + 1] - row0[g]);
-
-    // column groups, balanced by entries, boundaries on multiples of 64 columns
-    std::vector<long long> ccount((size_t)nc, 0);
-    for (long long i = 0; i < n; ++i)
-        if (len(i))
-            for (long long k = ptr[i]; k < ptr[i + 1]; ++k) ccount[col[k]]++;
-    std::vector<long long> cb{0};
-    {
-        long long cur = 0;
-        for (long long c = 0; c < nc && (int)cb.size() < q; ++c) {
-            cur += ccount[c];
-            if (cur * q >= nnz * (long long)cb.size() && (c + 1) % 64 == 0 && c + 1 < nc) cb.push_back(c + 1);
-        }
-        while ((int)cb.size() < q) cb.push_back(nc);  // empty trailing groups
-        cb.push_back(nc);
-    }
+    const std::vector<long long> cb = col_bounds(q);
     // stage geometry: px a multiple of 128 bytes, pe a multiple of 64 entries
     long long W = 64;
     for (int j = 0; j < q; ++j) W = std::max<long long>(W, cb[j + 1] - cb[j]);
@@ -537,7 +577,7 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
                                              int64_t *out_row, int64_t *out_col, uint32_t *out_val,
                                              int64_t *out_n, double *stats)
 {
-    if (nrows < 0 || ncols < 0 || !row_ptr || m < 2 || (q != 1 && q != 2 && q != 4) ||
+    if (nrows < 0 || ncols < 0 || !row_ptr || m < 2 || (q != 0 && q != 1 && q != 2 && q != 4) ||
         (nv != 1 && nv != 2 && nv != 4) || clusters < 1 || !out_n || cap < 0)
         return FFSPMV_ERR_ARG;
     const long long nnz = row_ptr[nrows];
@@ -551,7 +591,8 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
     }
     PanelHost H;
     const bool ok = panel_layout(nrows, ncols, (const long long *)row_ptr, c.data(), v.data(), cls.data(), m,
-                                 use_pm1 == 1, q, nv, [&](int cq, bool) { return cq == q ? clusters : 0; }, H);
+                                 use_pm1 == 1, q, nv,
+                                 [&](int cq, bool) { return q == 0 ? clusters / cq : cq == q ? clusters : 0; }, H);
     if (!ok) return FFSPMV_ERR_UNSUPPORTED;
     const int xb = H.tiny ? 1 : (H.small ? 2 : 4) * nv, ab = (H.small ? 4 : 8) * nv;  // bytes per column / per row
     long long n = 0, lanes = 0, packs = 0, bad_packs = 0;

@@ -93,6 +93,20 @@ def test_multi_vector_layout_limits():
         assert rc == want, (nv, rc)
 
 
+def test_builder_cluster_size_rule():
+    """The builder's choice between one and two CTAs per cluster (q = 0,
+    152 SMs): one for local structure (a band: each row group's entries fall
+    in one column half) and where the entries outweigh x in what a CTA
+    streams; two for spread columns with x at least twice the entries."""
+    n = 300_000
+    band = gen.banded_matrix(3, n, np.full(n, 12), 65521)
+    assert decode(band, 65521, 0, 0, 152)[3][9] == 1
+    sparse = gen.uniform_matrix(4, n, n, np.full(n, 4), 65521)          # x/e = 300k*2*152 / (1.2M*6) = 12.7
+    assert decode(sparse, 65521, 0, 0, 152)[3][9] == 2
+    dense = gen.uniform_matrix(5, 60_000, 60_000, np.full(60_000, 40), 65521)   # x/e = 60k*2*152 / (2.4M*6) = 1.3
+    assert decode(dense, 65521, 0, 0, 152)[3][9] == 1
+
+
 def test_layout_with_duplicates_zeros_and_long_rows():
     # repeated (i, j) pairs, explicit zeros, a row past the panel cap, empty rows
     rng = np.random.default_rng(5)
