@@ -236,6 +236,7 @@ struct PanelPart {
     bool on = false;
     bool small = true;   // m <= 2^16: u16 x and values, u32 row sums
     bool tiny = false;   // m <= 256, one vector per pass: u8 x and values, u32 row sums
+    bool mont = false;   // odd 2^16 < m < 2^31: values in Montgomery form (v 2^32 mod m)
     int nv = 1;          // vectors per pass: x and row sums interleaved by vector
     int q = 1;           // CTAs per cluster (column groups)
     int ngroup = 0;      // row groups

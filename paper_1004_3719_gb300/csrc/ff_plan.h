@@ -47,6 +47,7 @@ bool format_valid(int f, int bin, long long maxlen);
 struct PanelHost {
     bool small = true;
     bool tiny = false;  // m <= 256, one vector per pass: u8 x and values
+    bool mont = false;  // odd 2^16 < m < 2^31: values stored as v 2^32 mod m (Montgomery form)
     int nv = 1;
     int q = 1, ngroup = 0, rows_max = 0, resident = 0, px = 0, pe = 0, eb = 0;
     size_t smem = 0;

@@ -581,6 +581,46 @@ __device__ __forceinline__ void red_cluster_add(u32 addr, u64 v)
 // final reduction.
 __device__ __forceinline__ u32 red32_lazy(u32 t, u32 m, u32 mu) { return t - __umulhi(t, mu) * m; }
 
+// v x 2^-32 mod m, in [0, 2m), for odd m < 2^31, v < m and x < 2^32
+// (Montgomery, 1985).  With u = (v x mod 2^32)(-1/m) mod 2^32, v x + u m is
+// a multiple of 2^32: its low words add up to 0 (v x = 0 mod 2^32) or to
+// exactly 2^32, and (v x + u m) / 2^32 < (m 2^32 + 2^32 m) / 2^32 = 2m.
+// Values stored as v 2^32 mod m make this v x mod m.
+__device__ __forceinline__ u32 mont_red(u32 v, u32 x, u32 m, u32 mneg)
+{
+    const u32 lo = v * x, hi = __umulhi(v, x);
+    const u32 u = lo * mneg;
+    return hi + __umulhi(u, m) + (lo != 0u ? 1u : 0u);
+}
+
+// -1/m mod 2^32 for odd m: y <- y (2 - m y) doubles the number of correct
+// low bits (Newton's iteration for the inverse), starting from y = m, which
+// is right to 3 bits (m m = 1 mod 8 for odd m).
+__device__ __forceinline__ u32 neg_inv32(u32 m)
+{
+    u32 y = m;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y *= 2u - m * y;
+    return 0u - y;
+}
+
+// Row sums in shared memory.  A u32 sum takes one reduction.  A 64-bit word
+// holds two u32 sums, added as two 32-bit reductions (a 64-bit shared-memory
+// atomic add costs far more): for m > 2^16 the sums of the low 16 bits (low
+// word) and of the rest (high word) of every value added, the row's sum being
+// low + 2^16 high; for two 16-bit-residue vectors, one vector's sum per word.
+template <bool SPLIT16>
+__device__ __forceinline__ void row_add(u64 *p, u64 c)
+{
+    u32 *w = reinterpret_cast<u32 *>(p);
+    atomicAdd(w, SPLIT16 ? (u32)c & 0xffffu : (u32)c);
+    atomicAdd(w + 1, (u32)(c >> (SPLIT16 ? 16 : 32)));
+}
+template <bool SPLIT16>
+__device__ __forceinline__ void row_add(u32 *p, u32 c) { atomicAdd(p, c); }
+__device__ __forceinline__ u64 row_total(u64 w) { return (w & 0xffffffffull) + ((w >> 32) << 16); }
+__device__ __forceinline__ u64 row_total(u32 w) { return w; }
+
 __device__ __forceinline__ void mbar_init(u32 bar, u32 count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -675,12 +715,19 @@ struct PanelX {
 // y = alpha A x + beta y for NV vectors at once (x: columns vcol..vcol+NV-1
 // of the block, interleaved in the staged copy; row sums [row][NV]).  TINY
 // (m <= 256, NV = 1): x and values as u8, terms v x < 2^16 added unreduced.
-template <bool SMALL, int NV, bool TINY = false>
+// MONT (odd 2^16 < m < 2^31): values in Montgomery form, terms v x mod m
+// in [0, 2m) by one Montgomery reduction.  For m > 2^16 every row sum is
+// a pair of u32 sums (row_add): each row's terms (below 2^32) number at most
+// kPanelLong = 2^15, so the low-16-bit sum stays below 2^15 2^16 = 2^31 and
+// the high sum below 2^15 2^32 / 2^16 = 2^31, however the terms are grouped
+// into pack sums, CTAs and cluster partial sums.
+template <bool SMALL, int NV, bool TINY = false, bool MONT = false>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__restrict__ y, long long ldy,
         const Mod M, int *status, int skip_stage, int conv)
 {
     static_assert(!TINY || (SMALL && NV == 1), "u8 x: one vector, m <= 256");
+    static_assert(!MONT || !SMALL, "Montgomery terms: m > 2^16");
     typedef typename std::conditional<TINY, unsigned char,
                                       typename std::conditional<SMALL, unsigned short, u32>::type>::type XT;
     typedef typename std::conditional<SMALL, u32, u64>::type AT;
@@ -866,6 +913,7 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
         }
     } else {
         const u32 mu32 = (u32)(M.mu >> 32);  // floor(2^32 / m)
+        const u32 mneg = MONT ? neg_inv32(M.m) : 0u;
         const u32 rot = ((u32)P.pe / 8u + 31u) / 32u;  // blocks of a full stage
         for (u32 s = 0; s < ns; ++s) {
             const u32 b = s % kPanelStages;
@@ -926,7 +974,8 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                                 for (int u = 0; u < 8; ++u) {
                                     const u32 xv = *reinterpret_cast<const XT *>(xs + (e[u] & kPanelIdxMask) * sizeof(XT));
                                     tm[u] = TINY ? (AT)(v[u] * xv)
-                                                 : SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32) : (AT)red64((u64)v[u] * xv, M);
+                                                 : SMALL ? (AT)red32_lazy(v[u] * xv, M.m, mu32)
+                                                 : MONT ? (AT)mont_red(v[u], xv, M.m, mneg) : (AT)red64((u64)v[u] * xv, M);
                                 }
                             } else {
                                 // +-1 sections (Sec. 2.4.2): x or m - x, no value
@@ -962,11 +1011,11 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                                 if (lane + d < 32 && k2 == key) sum += o;
                             }
                             const u32 kp = __shfl_up_sync(0xffffffffu, key, 1);
-                            if (pack && (lane == 0 || kp != key)) atomicAdd(acc + (key & 0xffffu), sum);
+                            if (pack && (lane == 0 || kp != key)) row_add<!SMALL>(acc + (key & 0xffffu), sum);
                         }
                         if (valid && !pack) {
     #pragma unroll
-                            for (int u = 0; u < 8; ++u) atomicAdd(acc + (e[u] >> 16), tm[u]);
+                            for (int u = 0; u < 8; ++u) row_add<!SMALL>(acc + (e[u] >> 16), tm[u]);
                         }
                     } else {
                         const u32 tl = lb + lane, c = min(32u, nl - lb);
@@ -1035,8 +1084,9 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                                     for (int h = 0; h < VG; ++h) {
                                         const u32 xv = XC::get(xw[u], k + h);
                                         // +-1 sections (Sec. 2.4.2): x or m - x, no value
-                                        const LT t1 = general ? (SMALL ? (LT)red32_lazy(v[u] * xv, M.m, mu32)
-                                                                       : (LT)red64((u64)v[u] * xv, M))
+                                        const LT t1 = general ? (SMALL  ? (LT)red32_lazy(v[u] * xv, M.m, mu32)
+                                                                 : MONT ? (LT)mont_red(v[u], xv, M.m, mneg)
+                                                                        : (LT)red64((u64)v[u] * xv, M))
                                                               : (LT)((e[u] & kPanelNeg) ? M.m - xv : xv);
                                         tv |= t1 << (32 * h);
                                     }
@@ -1059,11 +1109,11 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
                                     const LT o = __shfl_down_sync(0xffffffffu, sum, 1 << i);
                                     if (seg & (1u << i)) sum += o;
                                 }
-                                if (head) atomicAdd(reinterpret_cast<LT *>(acc + (e[0] >> 16) * NV + k), sum);
+                                if (head) row_add<!SMALL>(reinterpret_cast<LT *>(acc + (e[0] >> 16) * NV + k), sum);
                             }
                             if (valid && !pack) {
     #pragma unroll
-                                for (int u = 0; u < 8; ++u) atomicAdd(reinterpret_cast<LT *>(acc + (e[u] >> 16) * NV + k), tm[u]);
+                                for (int u = 0; u < 8; ++u) row_add<!SMALL>(reinterpret_cast<LT *>(acc + (e[u] >> 16) * NV + k), tm[u]);
                             }
                         }
                     }
@@ -1104,7 +1154,13 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
             const u32 base = map_cluster(acc, (u32)j);
             for (u32 f = jb + t; f < je; f += kPanelThreads) {
                 const AT v = acc[f];
-                if (v) red_cluster_add(base + f * (u32)sizeof(AT), v);
+                // a pair of u32 sums adds word by word (no carry crosses)
+                if constexpr (SMALL) {
+                    if (v) red_cluster_add(base + f * (u32)sizeof(AT), v);
+                } else {
+                    if ((u32)v) red_cluster_add(base + f * (u32)sizeof(AT), (u32)v);
+                    if ((u32)(v >> 32)) red_cluster_add(base + f * (u32)sizeof(AT) + 4u, (u32)(v >> 32));
+                }
             }
         }
         cluster_sync_all();  // every partial sum of this CTA's share has arrived
@@ -1112,16 +1168,17 @@ k_panel(const PanelPart P, const u32 *__restrict__ x, long long ldx, u32 *__rest
     const u32 rb = min(nf, rank * share), re = min(nf, rb + share);
     for (u32 f = rb + t; f < re; f += kPanelThreads) {
         u32 *yp = y + (long long)(r0 + f / NV) * ldy + f % NV;
-        *yp = combine(red64((u64)acc[f], M), yp, false, M);
+        *yp = combine(red64(row_total(acc[f]), M), yp, false, M);
     }
 }
 
 // The panel kernel instance for (16-bit residues, vectors per pass).
 typedef void (*PanelKernel)(const PanelPart, const u32 *, long long, u32 *, long long, const Mod, int *, int, int);
-static PanelKernel panel_kernel(bool small, int nv, bool tiny = false)
+static PanelKernel panel_kernel(bool small, int nv, bool tiny = false, bool mont = false)
 {
     if (tiny) return k_panel<true, 1, true>;
     if (small) return nv == 4 ? k_panel<true, 4> : nv == 2 ? k_panel<true, 2> : k_panel<true, 1>;
+    if (mont) return nv == 2 ? k_panel<false, 2, false, true> : k_panel<false, 1, false, true>;
     return nv == 2 ? k_panel<false, 2> : k_panel<false, 1>;
 }
 
@@ -1179,7 +1236,7 @@ static ffspmv_status run_panel(const Plan &P, const u32 *x, long long ldx, u32 *
         else k_x_stage<u32, 1><<<sb, 256, 0, st>>>(x + vcol, ldx, P.ncols, xs32);
         FF_CUDA(cudaGetLastError());
     }
-    const PanelKernel kf = panel_kernel(pp.small, pp.nv, pp.tiny);
+    const PanelKernel kf = panel_kernel(pp.small, pp.nv, pp.tiny, pp.mont);
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(pp.ngroup * pp.q), 1, 1);

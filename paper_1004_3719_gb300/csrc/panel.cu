@@ -316,6 +316,9 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     if (n <= 0 || nc <= 0 || nnz == 0 || nnz >= (1LL << 31) || nc >= (1LL << 31) - 65536) return false;
     const bool small = m <= 65536u;
     const bool tiny = m <= 256u && nv == 1;  // u8 x and values (one vector per pass)
+    // odd m in (2^16, 2^31): each value v is stored as v 2^32 mod m, so that
+    // the kernel's Montgomery reduction of v' x gives v x mod m (in [0, 2m))
+    const bool mont = !small && (m & 1u) != 0 && m < 0x80000000u;
     if (nv != 1 && nv != 2 && !(nv == 4 && small)) return false;
     // bytes of x per column and of row sums per row: nv vectors interleaved
     const int xb = tiny ? 1 : (small ? 2 : 4) * nv, vb = tiny ? 1 : small ? 2 : 4, ab = (small ? 4 : 8) * nv;
@@ -454,7 +457,8 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
                     const long long xoff = cb[cgrp[c]] + (pan - pbase[cgrp[c]]) * pcols;
                     const long long at = pos[g * npan + pan]++;
                     const bool pm = pm_on && cls[k] != 0;
-                    bent[at] = SEnt{(u32)(i - row0[g]), (u32)(c - xoff), val[k], cls[k] == kMinus ? 1u : 0u};
+                    const u32 v = mont ? (u32)(((unsigned long long)val[k] << 32) % m) : val[k];
+                    bent[at] = SEnt{(u32)(i - row0[g]), (u32)(c - xoff), v, cls[k] == kMinus ? 1u : 0u};
                     bpm[at] = pm ? 1 : 0;
                 }
             }
@@ -551,6 +555,7 @@ bool panel_layout(long long n, long long nc, const long long *ptr, const u32 *co
     }
     H.small = small;
     H.tiny = tiny;
+    H.mont = mont;
     H.nv = nv;
     H.q = q;
     H.ngroup = (int)ng;
@@ -595,6 +600,17 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
                                  [&](int cq, bool) { return q == 0 ? clusters / cq : cq == q ? clusters : 0; }, H);
     if (!ok) return FFSPMV_ERR_UNSUPPORTED;
     const int xb = H.tiny ? 1 : (H.small ? 2 : 4) * nv, ab = (H.small ? 4 : 8) * nv;  // bytes per column / per row
+    // values in Montgomery form decode through the inverse of 2^32 mod m
+    // (extended Euclid on (2^32 mod m, m); m is odd there, so it exists)
+    unsigned long long rinv = 1;
+    if (H.mont) {
+        long long r0 = (long long)m, r1 = (long long)((1ull << 32) % m), t0 = 0, t1 = 1;
+        while (r1 != 0) {
+            const long long qt = r0 / r1, r2 = r0 - qt * r1, t2 = t0 - qt * t1;
+            r0 = r1; r1 = r2; t0 = t1; t1 = t2;
+        }
+        rinv = (unsigned long long)((t0 % (long long)m + (long long)m) % (long long)m);
+    }
     long long n = 0, lanes = 0, packs = 0, bad_packs = 0;
     double gwf = 0, awf = 0, slots = 0, aslots = 0;
     for (long long cta = 0; cta < (long long)H.ngroup * H.q; ++cta) {
@@ -619,6 +635,7 @@ extern "C" ffspmv_status ffspmv_panel_decode(int64_t nrows, int64_t ncols, const
                         if (general) {
                             const int vpos = H.small ? 8 * t + u : 8 * b0 + (u < 4 ? 4 * j + u : 4 * cg + 4 * j + (u - 4));
                             value = H.val[st.v0 + vpos];
+                            if (H.mont) value = (u32)((unsigned long long)value * rinv % m);
                         } else {
                             value = (w[u] & kPanelNeg) ? m - 1u : 1u;
                         }

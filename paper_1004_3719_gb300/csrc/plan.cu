@@ -665,6 +665,7 @@ bool make_panel(Blob &B, const Mat &A, u32 m, int use_pm1, int force_q, int nv, 
     pp.on = true;
     pp.small = H.small;
     pp.tiny = H.tiny;
+    pp.mont = H.mont;
     pp.nv = H.nv;
     pp.q = H.q;
     pp.ngroup = H.ngroup;
@@ -933,7 +934,7 @@ ffspmv_status build_plan_ex(Plan &P, long long nrows, long long ncols,
                  " + %d entries, x staged as %s, %s row sums, %d vector(s) per pass, %lld entries in +-1 sections,"
                  " %lld padding\n",
                  P.panel.ngroup, P.panel.q, P.panel.q, P.panel.resident, P.panel.nstage, P.panel.px, P.panel.pe,
-                 P.panel.tiny ? "u8" : P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : "u64", P.panel.nv, P.panel.npm,
+                 P.panel.tiny ? "u8" : P.panel.small ? "u16" : "u32", P.panel.small ? "u32" : P.panel.mont ? "2 x u32 (Montgomery terms)" : "2 x u32", P.panel.nv, P.panel.npm,
                  P.panel.npad);
         P.summary += buf;
         return FFSPMV_OK;

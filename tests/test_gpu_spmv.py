@@ -99,7 +99,7 @@ def test_split_long_rows(lib):
                                  (2**31 - 1, 0), (2**31 - 1, 1), (2**31 - 1, 2)])
 def test_panel_column_groups(lib, m, q):
     # clusters of 1, 2 or 4 CTAs splitting the columns (0: the builder's
-    # choice; with u64 row sums four column groups leave no room); the
+    # choice; with 8-byte row sums four column groups leave no room); the
     # transpose has the power-law skew on its columns instead of its rows
     A = gen.powerlaw_matrix(seed=8, n=150_001, lmax=20_000, m=m, pm_fraction=0.2)
     M = make(lib, A, "PANEL", panel_cluster=q)
@@ -208,11 +208,13 @@ def test_panel_u8_moduli(lib, m):
     assert list(y) == [int(L) * (m - 1) * (m - 1) % m for L in lengths]
 
 
-@pytest.mark.parametrize("m,q", [(2**31 - 1, 1), (2**31 - 1, 2), (4294967291, 2), (65537, 4)])
+@pytest.mark.parametrize("m,q", [(2**31 - 1, 1), (2**31 - 1, 2), (4294967291, 2), (65537, 4), (2**20, 2)])
 def test_panel_wide_sums_at_worst_values(lib, m, q):
     """m > 2^16: every value and every x at m - 1, long rows split over the
-    column groups of a cluster (the CTAs' u64 partial sums meet in the
-    cluster epilogue); the results equal the closed form L (m-1)^2 mod m."""
+    column groups of a cluster (the CTAs' partial sums, pairs of u32 sums,
+    meet in the cluster epilogue); the results equal the closed form
+    L (m-1)^2 mod m.  Odd m < 2^31 takes Montgomery terms, 2^20 (even) and
+    4294967291 (above 2^31) the 64-bit Barrett reduction."""
     lengths = np.array([32_768, 20_000, 4097, 17, 1, 0, 3000])
     nc = 120_000
     rng = np.random.default_rng(q)
@@ -224,6 +226,34 @@ def test_panel_wide_sums_at_worst_values(lib, m, q):
     y = to_host(M.apply(to_dev(np.full(nc, m - 1, dtype=np.uint32))))
     assert list(y) == [int(L) * (m - 1) * (m - 1) % m for L in lengths]
     check_apply(lib, M, A, alpha=m - 2, beta=m - 3, seed=q)
+
+
+@pytest.mark.parametrize("m,q,nvec", [(4294967291, 1, 1), (4294967291, 2, 2), (2**31 - 1, 2, 1), (2**31 - 1, 1, 2)])
+def test_panel_split_row_sums_at_their_limit(lib, m, q, nvec):
+    """m > 2^16 keeps each row sum as two u32 sums, of the terms' low 16
+    bits and of the rest.  Rows of 32 768 entries (the most a row in the
+    panels has) with the largest terms the reduction gives: at 4294967291
+    every value m - 1 against x = 1, each term m - 1 = 2^32 - 6, so both
+    halves of the sum approach 2^31; at 2^31 - 1 (Montgomery terms below 2m)
+    values and x uniform.  Results against the closed form and the oracle,
+    for one- and two-vector passes."""
+    lengths = np.array([32_768, 32_768, 30_000, 1, 0, 32_767])
+    nc = 140_000
+    rng = np.random.default_rng(m % 1000 + q)
+    col = np.concatenate([np.sort(rng.choice(nc, L, replace=False)) for L in lengths]).astype(np.int32)
+    nnz = int(lengths.sum())
+    vals = (np.full(nnz, m - 1, dtype=np.uint32) if m > 2**31
+            else rng.integers(1, m, nnz, dtype=np.uint64).astype(np.uint32))
+    A = gen.CSR(lengths.size, nc, np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64), col, vals, m)
+    hooks = 4 if nvec > 1 else 0   # test hook 4: keep the 2-vector layout
+    M = make(lib, A, "PANEL", panel_cluster=q, use_pm1=0, transpose_mode=lib.TRANSPOSE.NONE, test_hooks=hooks)
+    assert "panels:" in M.describe()
+    if m > 2**31:
+        X = np.ones((nc, nvec), dtype=np.uint32)
+        Y = to_host(M.apply(to_dev(X if nvec > 1 else X[:, 0]))).reshape(lengths.size, nvec)
+        for k in range(nvec):
+            assert list(Y[:, k]) == [int(L) * (m - 1) % m for L in lengths]
+    check_apply(lib, M, A, nvec=nvec, alpha=m - 2, beta=m - 3, seed=q + nvec)
 
 
 def test_panel_wide_passes_kept_only_when_faster(lib):

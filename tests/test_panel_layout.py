@@ -49,8 +49,11 @@ def same_triples(a, b):
 
 
 @pytest.mark.parametrize("m,use_pm1,q", [(65521, 0, 2), (65521, 1, 2), (3, 1, 2), (3, 0, 4),
-                                         (2**31 - 1, 1, 2), (2**31 - 1, 0, 1), (65536, 1, 4)])
+                                         (2**31 - 1, 1, 2), (2**31 - 1, 0, 1), (65536, 1, 4),
+                                         (2**20, 1, 2), (4294967291, 0, 1)])
 def test_layout_decodes_to_the_matrix(m, use_pm1, q):
+    # odd 2^16 < m < 2^31 stores values in Montgomery form (v 2^32 mod m);
+    # the decoder maps them back, so every modulus decodes to the matrix
     A = with_modulus(gen.powerlaw_matrix(seed=41, n=60_000, lmax=6000), m, pm_fraction=0.3, seed=3)
     r, c, v, st = decode(A, m, use_pm1, q, 12)
     assert st[8] == 0                                   # every pack is one row
