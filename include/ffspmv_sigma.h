@@ -74,6 +74,29 @@ ffspmv_status sigma_basis(uint32_t p, int32_t m, int32_t n, int64_t d, int32_t b
 ffspmv_status sigma_wiedemann_input(uint32_t p, int32_t s, int64_t L, const uint32_t *d_S, uint32_t *d_F,
                                     ffspmv_stream_t stream);
 
+/*
+ * deg det U and codeg det U (the multiplicity of x in det U) of the
+ * generator of a sigma-basis: U = the n rows of d_P with the least
+ * (h_delta_i, i), columns 0..n-1, an n x n polynomial matrix.  For the
+ * block-Wiedemann input [S(x); -I_s] (n = s), deg det U - codeg det U is the
+ * rank of a suitably preconditioned A (Sec. 3, step 3; Sec. 3.3, determinant
+ * co-degree).  d_P: device, (d+1) x m x m as sigma_basis writes it; h_delta:
+ * host, the m degrees sigma_basis returns (only their order is used).  p a
+ * prime, 2 <= p <= 2^31; 1 <= n <= m <= 32; d >= 0.  Both values are x-adic
+ * valuations of determinants (codeg det U = v(det U); deg det U = sum_r D_r -
+ * v(det U~), D_r the degree of row r of U and U~ its rows reversed against
+ * D_r), each read off Gaussian elimination over F_p[[x]] truncated at x^K
+ * with pivots of least valuation, on the device; K starts at 32 and doubles
+ * until every pivot is found below the precision, up to max_precision (0 =
+ * 4096; at most 65536).  Returns FFSPMV_ERR_UNSUPPORTED when det U = 0 (a
+ * zero row, or no pivot below max_precision).  Allocates its working memory
+ * (n^2 K words) on the current device and is synchronous (it reads each
+ * column's pivot valuations back); results in *h_deg, *h_codeg (host).
+ */
+ffspmv_status sigma_generator_degrees(uint32_t p, int32_t m, int32_t n, int64_t d, const uint32_t *d_P,
+                                      const int32_t *h_delta, int32_t max_precision, int64_t *h_deg,
+                                      int64_t *h_codeg, ffspmv_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

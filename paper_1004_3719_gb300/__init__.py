@@ -26,7 +26,8 @@ from ._api import (Matrix, spmv_apply, spmv_apply_transpose,  # noqa: F401
                    spmv_apply_transpose_noalloc,
                    spmv_batch_apply, spmv_block_project, spmv_block_project_finish,
                    spmv_block_sequence, spmv_create_hybrid,
-                   polymat_mul, sigma_basis, sigma_wiedemann_input, spmv_apply_gf2, spmv_check_status,
+                   polymat_mul, sigma_basis, sigma_generator_degrees, sigma_wiedemann_input,
+                   spmv_apply_gf2, spmv_check_status,
                    spmv_count_launches, spmv_describe_plan,
                    spmv_destroy, spmv_get_info, stream_ptr, to_numpy_u32)
 
@@ -36,7 +37,8 @@ __all__ = ["build", "Matrix", "Options", "FMT", "SEL", "TRANSPOSE", "FFSPMVError
            "spmv_block_sequence", "spmv_block_project", "spmv_block_project_finish",
            "spmv_batch_apply", "spmv_destroy",
            "spmv_describe_plan", "spmv_get_info", "spmv_count_launches",
-           "spmv_check_status", "spmv_apply_gf2", "polymat_mul", "sigma_basis", "sigma_wiedemann_input",
+           "spmv_check_status", "spmv_apply_gf2", "polymat_mul", "sigma_basis", "sigma_generator_degrees",
+           "sigma_wiedemann_input",
            "options_default", "to_numpy_u32",
            "status_string", "library_path"]
 

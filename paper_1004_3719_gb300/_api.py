@@ -177,6 +177,24 @@ def sigma_basis(p, F, shift=None, base=0, stream=None):
     return P, [int(v) for v in delta], int(deg.value)
 
 
+def sigma_generator_degrees(p, P, delta, n, max_precision=0, stream=None):
+    """(deg det U, codeg det U) of the generator U of a sigma-basis: the n
+    rows of P (a (d + 1, m, m) array, device or numpy) with the least
+    (delta_i, i), first n columns.  deg - codeg is block Wiedemann's rank."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P = _as_u32_tensor(P, dev)
+    d1, m = P.shape[0], P.shape[1]
+    dl = np.ascontiguousarray(delta, dtype=np.int32)
+    if dl.size != m:
+        raise ValueError("delta needs one degree per row of P")
+    deg, codeg = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().sigma_generator_degrees(int(p), m, int(n), d1 - 1, _ptr(P), _ptr(dl), int(max_precision),
+                                        ctypes.byref(deg), ctypes.byref(codeg), stream_ptr(stream)),
+          "sigma_generator_degrees")
+    return int(deg.value), int(codeg.value)
+
+
 def sigma_wiedemann_input(p, S, stream=None):
     """[S(x); -I] as a (L, 2s, s) device tensor, from the (L, s, s) block
     sequence S (device or numpy)."""

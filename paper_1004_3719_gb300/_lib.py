@@ -96,6 +96,9 @@ def _declare(L):
     L.sigma_basis.restype = ctypes.c_int
     L.sigma_wiedemann_input.argtypes = [_U32, _I32, _I64, _P, _P, _P]
     L.sigma_wiedemann_input.restype = ctypes.c_int
+    L.sigma_generator_degrees.argtypes = [_U32, _I32, _I32, _I64, _P, _P, _I32, ctypes.POINTER(_I64),
+                                          ctypes.POINTER(_I64), _P]
+    L.sigma_generator_degrees.restype = ctypes.c_int
     L.spmv_block_project.argtypes = [_U32, _I64, _I32, _P, _P, _P, _P]
     L.spmv_block_project.restype = ctypes.c_int
     L.spmv_block_project_finish.argtypes = [_U32, _I32, _P, _P, _P]

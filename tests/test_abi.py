@@ -68,6 +68,14 @@ def test_host_side_argument_errors_without_gpu():
     assert L.sigma_basis(65521 * 3, 2, 1, 4, 0, 8, None, 8, ctypes.byref(d), None, 16, 1 << 20, None) == 1  # p prime
     assert L.sigma_basis(65521, 2, 1, 4, 0, None, None, 8, ctypes.byref(d), None, 16, 1 << 20, None) == 1   # pointers
     assert L.sigma_wiedemann_input(65521, 17, 4, 8, 8, None) == 1           # s <= 16
+    dg, cd = ctypes.c_int64(), ctypes.c_int64()
+    dl = (ctypes.c_int32 * 4)(0, 0, 0, 0)
+    gd = L.sigma_generator_degrees
+    assert gd(65521 * 3, 4, 2, 3, 8, dl, 0, ctypes.byref(dg), ctypes.byref(cd), None) == 1   # p prime
+    assert gd(65521, 4, 5, 3, 8, dl, 0, ctypes.byref(dg), ctypes.byref(cd), None) == 1       # n <= m
+    assert gd(65521, 33, 2, 3, 8, dl, 0, ctypes.byref(dg), ctypes.byref(cd), None) == 1      # m <= 32
+    assert gd(65521, 4, 2, 3, None, dl, 0, ctypes.byref(dg), ctypes.byref(cd), None) == 1    # pointers
+    assert gd(65521, 4, 2, 3, 8, dl, 1 << 17, ctypes.byref(dg), ctypes.byref(cd), None) == 1  # precision <= 2^16
     assert ff.status_string(6) == "device wait timed out"
     o = ff.options_default()
     assert o.use_pm1 == -1 and o.ell_width == -1 and o.transpose_mode == 0

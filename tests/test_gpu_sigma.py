@@ -106,6 +106,8 @@ def test_block_wiedemann_pipeline_rank(lib):
     U = sigma.trim(P[:, rows, :s].astype(object))
     dg, cdg = sigma.degree_and_codegree(sigma.det_poly(U, p))
     assert dg - cdg == n - 2 * z
+    # the library's own deg det and codeg det of the GPU generator
+    assert lib.sigma_generator_degrees(p, P.astype(np.uint32), delta, s) == (dg, cdg)
 
 
 def _coeff_np(P, F, k, e):
@@ -170,6 +172,8 @@ def test_wiedemann_100k_generator(lib):
     lead = np.stack([P[delta[i], i, :s] for i in rows])
     assert _det_mod(lead, p) != 0                   # row reduced: deg det = N
     assert _det_mod(P[0][rows][:, :s], p) != 0      # codegree 0: rank N
+    # the library reads the same rank off the device basis
+    assert lib.sigma_generator_degrees(p, Pd, delta, s) == (N, 0)
 
 
 def test_errors(lib):
