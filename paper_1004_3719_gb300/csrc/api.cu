@@ -64,9 +64,9 @@ void destroy_handle(ffspmv_handle *h)
 // the binned one on every measured shape: at least 2^21 entries (enough to
 // fill the stage pipelines of all SMs) and at least 3 entries per column
 // (each column of x streamed through shared memory serves several entries),
-// at any modulus (u64 row sums at m > 2^16: 93 vs 101 us on the 1M power-law
-// matrix, 106-158 vs 211-246 us on held-out 34M-entry matrices).  Elsewhere
-// AUTO is BINNED.
+// at any modulus (m > 2^16, 8-byte row sums: 61-67 vs 101 us on the 1M
+// power-law matrix; 106-158 vs 211-246 us on held-out 34M-entry matrices when
+// those sums were still u64 atomics).  Elsewhere AUTO is BINNED.
 bool panel_preferred(long long ncols, long long nnz, u32 m)
 {
     (void)m;
