@@ -144,3 +144,46 @@ def test_degrees_are_minimal_by_enumeration(p, m, n, d, shift, seed):
         for D in range(0, 3):
             want = p ** sum(max(0, D - dl + 1) for dl in delta)
             assert _count_approximants(F, d, shift, D, p) == want, (D, delta)
+
+
+def _pmul(a, b, p):
+    out = [0] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        for j, y in enumerate(b):
+            out[i + j] = (out[i + j] + x * y) % p
+    return out
+
+
+@pytest.mark.parametrize("n,e,seed", [(1, 4, 1), (3, 2, 2), (4, 3, 3)])
+def test_det_poly_of_triangular_matrices(n, e, seed):
+    # det of a triangular polynomial matrix is the product of its diagonal
+    # (by plain polynomial multiplication); rows shifted by powers of x give
+    # a nonzero codegree
+    p = 10007
+    rng = np.random.default_rng(seed)
+    P = np.zeros((e + 1, n, n), dtype=object)
+    for i in range(n):
+        for j in range(i, n):
+            P[:, i, j] = [int(v) for v in rng.integers(0, p, e + 1)]
+    P[0, 0, 0] = 0                       # x divides the first diagonal entry
+    want = [1]
+    for i in range(n):
+        want = _pmul(want, [int(P[k, i, i]) for k in range(e + 1)], p)
+    got = sigma.det_poly(P, p)
+    assert got[:len(want)] == want and not any(got[len(want):])
+    dg, cdg = sigma.degree_and_codegree(got)
+    assert cdg >= 1
+
+
+def test_det_poly_2x2_closed_form():
+    # det [[a, b], [c, d]] = a d - b c, by plain polynomial multiplication
+    p = 65521
+    rng = np.random.default_rng(7)
+    a, b, c, d = ([int(v) for v in rng.integers(0, p, 4)] for _ in range(4))
+    P = np.zeros((4, 2, 2), dtype=object)
+    for k in range(4):
+        P[k] = [[a[k], b[k]], [c[k], d[k]]]
+    ad, bc = _pmul(a, d, p), _pmul(b, c, p)
+    want = [(x - y) % p for x, y in zip(ad, bc)]
+    got = sigma.det_poly(P, p)
+    assert got[:len(want)] == want and not any(got[len(want):])
