@@ -260,11 +260,19 @@ ffspmv_status gd_alloc(GdRun &G, int K)
 {
     gd_free(G);
     const size_t ints = 3 * (size_t)kGdMaxN * sizeof(int);
-    FF_CUDA(cudaMalloc(&G.d_sel, ints));
+    if (cudaMalloc(&G.d_sel, ints) != cudaSuccess) {
+        cudaGetLastError();
+        G.d_sel = nullptr;
+        return FFSPMV_ERR_OOM;
+    }
     G.d_rowdeg = G.d_sel + kGdMaxN;
     G.d_val = G.d_sel + 2 * kGdMaxN;
     const size_t words = (size_t)G.n * G.n * K + (size_t)G.n * K + (size_t)K;
-    FF_CUDA(cudaMalloc(&G.W, words * sizeof(u32)));
+    if (cudaMalloc(&G.W, words * sizeof(u32)) != cudaSuccess) {
+        cudaGetLastError();
+        G.W = nullptr;
+        return FFSPMV_ERR_OOM;
+    }
     G.F = G.W + (size_t)G.n * G.n * K;
     G.inv = G.F + (size_t)G.n * K;
     G.cap = K;
