@@ -91,8 +91,8 @@ ffspmv_status sigma_wiedemann_input(uint32_t p, int32_t s, int64_t L, const uint
  * 4096; at most 65536).  Returns FFSPMV_ERR_UNSUPPORTED when det U = 0 (a
  * zero row, or no pivot below max_precision).  Allocates its working memory
  * (n^2 K words) on the current device, where d_P must live (FFSPMV_ERR_OOM
- * when that fails), and is synchronous (it reads each
- * column's pivot valuations back); results in *h_deg, *h_codeg (host).
+ * when that fails), and is synchronous (it reads each column's pivot
+ * valuations back); results in *h_deg, *h_codeg (host).
  */
 ffspmv_status sigma_generator_degrees(uint32_t p, int32_t m, int32_t n, int64_t d, const uint32_t *d_P,
                                       const int32_t *h_delta, int32_t max_precision, int64_t *h_deg,
